@@ -1,0 +1,320 @@
+"""Pins for the FP64 CPU oracle (no GPU).
+
+The oracle (oracle/ws_oracle.c) is checked against things the paper and the
+mathematics fix, none of which re-run the oracle's own algorithm:
+brute-force minimisation over ordered partitions, the subgradient optimality
+certificate (Eq. prox_opt + Eq. subdiff_R), the textbook min-max formula of
+isotonic regression, printed worked examples, closed forms, Prop. 3.2 / 4.1,
+Cor. D.5, and the worst-case generators of Sec. 4.1.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import pins
+from paper_2311_03096_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_kv(name):
+    kv = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, *v = line.split()
+            kv[k] = [float(t) for t in v]
+    return kv
+
+
+def test_kearsley_worked_example():
+    kv = _read_kv("kearsley.txt")
+    lam = kv["lambda"][0]
+    w = np.array(kv["w"])
+    # the fixture's y is w plus the shift of Alg. 2
+    np.testing.assert_allclose(w + lam * pins.shift_coefficients(4), kv["y"], atol=1e-15)
+    out, ids, nc = oracle.prox(w, lam)
+    np.testing.assert_allclose(out, kv["out"], atol=1e-15)
+    assert ids.tolist() == [int(t) for t in kv["ids"]]
+    assert nc == 3
+
+
+def test_hyperplanes_d3_example():
+    rows, printed = [], []
+    with open(os.path.join(GOLDEN, "hyperplanes_d3.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            if parts[0] == "set":
+                printed.append(tuple(int(t) for t in parts[1:]))
+            else:
+                order = [int(t) - 1 for t in parts[0].split(",")]
+                rows.append((order, [int(t) for t in parts[1:]]))
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        w = rng.standard_normal(3)
+        for order, c in rows:
+            assert pins.hyperplane(w, order) == pytest.approx(float(np.dot(c, w)), abs=1e-14)
+        r_eq1 = pins.R_pairs_py(list(w))
+        assert oracle.R_pairs(w) == pytest.approx(r_eq1, abs=1e-14)
+        assert max(float(np.dot(c, w)) for c in printed) == pytest.approx(r_eq1, abs=1e-14)
+        # the maximising hyperplanes are exactly those of sorting permutations (Sec. 2)
+        srt = list(np.argsort(w))
+        best = max(rows, key=lambda oc: float(np.dot(oc[1], w)))
+        assert best[0] == srt
+    assert sorted(printed) == sorted(tuple(c) for _, c in rows)
+
+
+@pytest.mark.parametrize("d", [2, 3, 5, 17, 200])
+def test_R_sorted_form_matches_definition(d):
+    rng = np.random.default_rng(d)
+    w = rng.standard_normal(d)
+    w[: d // 3] = w[0]  # ties
+    ref = pins.R_pairs_py(list(w))
+    assert oracle.R_pairs(w) == pytest.approx(ref, rel=1e-12, abs=1e-12)
+    assert oracle.R_sorted(w) == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
+def _small_cases():
+    rng = np.random.default_rng(11)
+    cases = []
+    for d in range(1, 7):
+        for lam in (0.0, 0.05, 0.3, 1.0, 10.0):
+            cases.append((rng.standard_normal(d), lam))
+            w = np.round(rng.standard_normal(d), 1)  # frequent exact ties
+            cases.append((w, lam))
+    return cases
+
+
+@pytest.mark.parametrize("w,lam", _small_cases())
+def test_brute_force_small(w, lam):
+    u_bf, _ = pins.brute_force_prox(list(w), lam)
+    out, ids, nc = oracle.prox(w, lam)
+    np.testing.assert_allclose(out, u_bf, atol=1e-10)
+    # the partition: each cluster is a level set of the output; two clusters
+    # may share a value only on a near-tie (real-valued equal means that
+    # rounding separates), and the exact rational PAV of the same FP inputs
+    # gives the same partition
+    order = np.argsort(out, kind="stable")
+    assert np.all(np.diff(ids[order]) >= 0)
+    for c in range(nc):
+        assert np.ptp(out[ids == c]) == 0.0
+    _, exact_ids = pins.exact_prox_fraction(list(w), lam)
+    assert ids.tolist() == exact_ids
+
+
+def test_brute_force_d7():
+    rng = np.random.default_rng(7)
+    w = rng.standard_normal(7)
+    for lam in (0.2, 1.5):
+        u_bf, _ = pins.brute_force_prox(list(w), lam)
+        out, _, _ = oracle.prox(w, lam)
+        np.testing.assert_allclose(out, u_bf, atol=1e-10)
+
+
+def test_d2_closed_form():
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        w = rng.standard_normal(2) * 3
+        lam = float(rng.uniform(0, 3))
+        out, ids, nc = oracle.prox(w, lam)
+        lo, hi = (0, 1) if w[0] <= w[1] else (1, 0)
+        if w[hi] - w[lo] > 2 * lam:
+            exp = np.empty(2)
+            exp[lo], exp[hi] = w[lo] + lam, w[hi] - lam
+            assert nc == 2
+        else:
+            exp = np.full(2, w.mean())
+            assert nc == 1
+        np.testing.assert_allclose(out, exp, atol=1e-14)
+
+
+@pytest.mark.parametrize("d,lam", [(10, 0.1), (64, 0.5), (257, 0.02), (1000, 1.0), (1000, 0.001)])
+def test_optimality_certificate(d, lam):
+    rng = np.random.default_rng(d)
+    w = np.round(rng.standard_normal(d), 2)
+    out, _, _ = oracle.prox(w, lam)
+    assert pins.certificate_residual(w, out, lam) < 1e-9
+    # a perturbed output fails the certificate
+    bad = out.copy()
+    bad[rng.integers(d)] += 1e-3
+    assert pins.certificate_residual(w, bad, lam) > 1e-6
+
+
+def test_certificate_rejects_plausible_mistakes():
+    """The pins catch the mistakes an implementation could plausibly make:
+    the opposite sign of the shift, a 0-based range(d) and a dropped 1/(d-1)."""
+    rng = np.random.default_rng(5)
+    d, lam = 50, 0.4
+    w = rng.standard_normal(d)
+    out, _, _ = oracle.prox(w, lam)
+    assert pins.certificate_residual(w, out, lam) < 1e-9
+    x = np.sort(w)
+    order = np.argsort(w, kind="stable")
+    k = np.arange(1, d + 1)
+    wrong = {
+        "minus sign": x - lam * (d + 1 - 2 * k) / (d - 1),
+        "0-based range": x + lam * (d + 1 - 2 * (k - 1)) / (d - 1),
+        "no 1/(d-1)": x + lam * (d + 1 - 2 * k),
+    }
+    for name, y in wrong.items():
+        u = np.empty(d)
+        u[order] = pins.isotonic_minmax(y)
+        assert pins.certificate_residual(w, u, lam) > 1e-3, name
+
+
+@pytest.mark.parametrize("d", [8, 50, 200])
+def test_isotonic_minmax_formula(d):
+    rng = np.random.default_rng(d + 1)
+    w = rng.standard_normal(d)
+    for lam in (0.0, 0.1, 2.0):
+        out, _, _, perm, xs = oracle.prox(w, lam, return_perm=True)
+        y = xs + lam * pins.shift_coefficients(d)
+        np.testing.assert_allclose(out[perm], pins.isotonic_minmax(y), atol=1e-12)
+
+
+def test_invariants():
+    rng = np.random.default_rng(9)
+    for d in (2, 3, 100, 4096):
+        w = inputs.normal_with_duplicates(d, seed=d).astype(np.float64)
+        for lam in (0.0, 0.1, 1.0, 1000.0):
+            out, ids, nc, perm, xs = oracle.prox(w, lam, return_perm=True)
+            # Prop. 3.2: momentum is conserved, so the mean is preserved
+            assert out.mean() == pytest.approx(w.mean(), abs=1e-12 * (1 + abs(w).max() + lam))
+            # particles never cross (Sec. 4.2 item 1): output non-decreasing in sorted order
+            assert np.all(np.diff(out[perm]) >= 0)
+            assert np.all(np.diff(ids[perm]) >= 0) and ids[perm][0] == 0 and ids[perm][-1] == nc - 1
+            if lam == 0.0:
+                np.testing.assert_array_equal(out, w)
+                assert nc == len(np.unique(w))
+            lo, hi = pins.prop41_extremes(xs, lam)
+            assert out.min() == pytest.approx(lo, abs=1e-12 * (1 + lam))
+            assert out.max() == pytest.approx(hi, abs=1e-12 * (1 + lam))
+        lam_max = pins.collapse_threshold(np.sort(w))
+        assert oracle.prox(w, lam_max * (1 + 1e-9) + 1e-12)[2] == 1
+        if lam_max > 1e-9:
+            assert oracle.prox(w, lam_max * (1 - 1e-6))[2] > 1
+
+
+def test_neighbour_collision_corollary():
+    rng = np.random.default_rng(12)
+    for d, lam in ((30, 0.2), (300, 0.05), (300, 3.0)):
+        w = np.round(rng.standard_normal(d), 2)
+        out, ids, nc, perm, xs = oracle.prox(w, lam, return_perm=True)
+        for k in range(d - 1):
+            s = oracle.neighbour_slack(xs, lam, k)
+            same = ids[perm[k]] == ids[perm[k + 1]]
+            if abs(s) > 1e-12:
+                assert same == (s >= 0), (d, lam, k, s)
+
+
+def test_sort_total_order_and_stability():
+    w = np.array([1.0, -0.0, 0.0, -1.0, 1.0, 0.0, -0.0])
+    perm, xs = oracle.sort(w)
+    assert perm.tolist() == [3, 1, 6, 2, 5, 0, 4]
+
+
+@pytest.mark.parametrize("d", [2 ** 10, 2 ** 12, 2 ** 16])
+def test_cascade_generator(d):
+    """Sec. 4.1 worst case: everything merges into one cluster (merge count d-1),
+    and it takes about d/2 imminent-collision rounds (checked by a direct
+    simulation of Alg. 3's rounds for the smaller sizes)."""
+    w, lam = inputs.cascade(d)
+    out, ids, nc = oracle.prox(w, lam)
+    assert nc == 1
+    ws, lam2 = inputs.cascade(d, shuffle=True)
+    assert oracle.prox(ws, lam2)[2] == 1
+    if d <= 2 ** 12:
+        assert _ic_v2_rounds(np.sort(w.astype(np.float64)), lam) >= d // 2
+
+
+def _ic_v2_rounds(x, lam):
+    """Rounds of Alg. 3 (imminent collisions v2) on sorted x: a new cluster
+    starts where y[i-1] < y[i]; each round pools every maximal violating run."""
+    d = x.shape[0]
+    s = x + lam * pins.shift_coefficients(d)  # y per particle
+    m = np.ones(d)
+    ysum = s.copy()
+    rounds = 0
+    while True:
+        y = ysum / m
+        start = np.concatenate([[True], y[:-1] < y[1:]])
+        blk = np.cumsum(start) - 1
+        nb = blk[-1] + 1
+        rounds += 1
+        if nb == y.shape[0]:
+            return rounds
+        ysum = np.bincount(blk, weights=ysum, minlength=nb)
+        m = np.bincount(blk, weights=m, minlength=nb)
+
+
+@pytest.mark.parametrize("d", [2 ** 10, 2 ** 16])
+def test_mirror_generator(d):
+    w, lam = inputs.mirror(d, shuffle=True)
+    out, ids, nc = oracle.prox(w, lam)
+    assert nc == d // 2
+    assert np.all(np.bincount(ids) == 2)
+
+
+def test_backward_is_cluster_average_and_matches_fd():
+    rng = np.random.default_rng(4)
+    d, lam, eps = 64, 0.05, 1e-6
+    w = rng.standard_normal(d)
+    out, ids, nc = oracle.prox(w, lam)
+    assert 1 < nc < d
+    g = rng.standard_normal(d)
+    gin = oracle.backward(g, ids)
+    for c in range(nc):
+        m = ids == c
+        np.testing.assert_allclose(gin[m], g[m].mean(), atol=1e-14)
+    # central finite differences of <g, prox(w)>
+    fd = np.empty(d)
+    for i in range(d):
+        e = np.zeros(d)
+        e[i] = eps
+        fd[i] = (g @ oracle.prox(w + e, lam)[0] - g @ oracle.prox(w - e, lam)[0]) / (2 * eps)
+    np.testing.assert_allclose(fd, gin, atol=1e-6)
+
+
+def test_batched_equals_per_segment():
+    rng = np.random.default_rng(8)
+    lens = [0, 1, 2, 7, 100, 33]
+    parts = [rng.standard_normal(n) for n in lens]
+    off = np.concatenate([[0], np.cumsum(lens)])
+    lam = rng.uniform(0, 1, len(lens))
+    out, ids, nc = oracle.prox_batched(np.concatenate(parts), off, lam)
+    for s, p in enumerate(parts):
+        o, i, n = oracle.prox(p, lam[s])
+        np.testing.assert_array_equal(out[off[s]:off[s + 1]], o)
+        np.testing.assert_array_equal(ids[off[s]:off[s + 1]], i)
+        assert nc[s] == n
+
+
+def test_exact_rational_partition_agrees():
+    rng = np.random.default_rng(21)
+    for d in (3, 10, 40):
+        for lam in (0.01, 0.3):
+            w = np.round(rng.standard_normal(d), 1)
+            ref, ref_ids = pins.exact_prox_fraction(list(w), lam)
+            out, ids, _ = oracle.prox(w, lam)
+            assert ids.tolist() == ref_ids
+            np.testing.assert_allclose(out, [float(v) for v in ref], atol=1e-14)
+
+
+def test_error_paths():
+    with pytest.raises(oracle.OracleError):
+        oracle.prox(np.array([1.0, np.nan]), 0.1)
+    with pytest.raises(oracle.OracleError):
+        oracle.prox(np.array([1.0, np.inf]), 0.1)
+    with pytest.raises(oracle.OracleError):
+        oracle.prox(np.array([1.0, 2.0]), -0.1)
+    out, ids, nc = oracle.prox(np.zeros(0), 0.1)
+    assert nc == 0
+    out, ids, nc = oracle.prox(np.array([3.5]), 10.0)
+    assert out.tolist() == [3.5] and ids.tolist() == [0] and nc == 1
