@@ -1,0 +1,143 @@
+/*
+ * ws_prox.h -- C ABI of libws_prox.so: the proximal map of the weight-sharing
+ * penalty on NVIDIA GB300 (sm_103a).
+ *
+ * The penalty (Eq. (1) of "Weight-Sharing Regularization", arXiv 2311.03096):
+ *     R(w) = 1/(d-1) * sum_{i>j} |w_i - w_j|,   w in R^d.
+ * Its proximal map (Sec. 1, prox definition; unique by strong convexity):
+ *     prox_{lambda R}(w) = argmin_u  lambda R(u) + 1/2 ||u - w||^2.
+ * Computed as in Sec. 3-5 / Alg. 2: sort w ascending (x), shift
+ * y_k = x_k + lambda (d + 1 - 2k)/(d - 1) (k = 1..d, the particle velocity of
+ * Alg. 2), pool adjacent violators of y into clusters at their means (the
+ * isotonic regression of y, Sec. 3; pooling on >=, Sec. 4.1), and give every
+ * weight the value of its cluster.
+ *
+ * Conventions shared by every entry point:
+ *   - Data pointers (values, out, cluster ids, gradients, lambdas, cluster
+ *     counts) are DEVICE pointers owned by the caller, unless a parameter says
+ *     "host".  The library never frees them.
+ *   - All device scratch memory is owned by a ws_plan and allocated when the
+ *     plan is created; a call on an existing plan allocates nothing, never
+ *     synchronises the host and only enqueues work on `stream`, so it can be
+ *     captured in a CUDA graph.
+ *   - Layout: a batch is one flat array of n values; segment s is
+ *     values[offsets[s] .. offsets[s+1]), processed independently with its
+ *     own lambda.  Cluster ids are 0-based and local to their segment; id 0 is
+ *     the cluster of the smallest values and ids increase with the value.
+ *   - dtype WS_F32 means float values/out; WS_F64 means double values/out.
+ *     Cluster ids are int32.  out may alias values (in-place).
+ *   - Degenerate cases: a segment of length 0 is skipped; of length 1 gets
+ *     out = w and id 0; lambda = 0 gives out = w with one cluster per distinct
+ *     value.  Ties in w always share a cluster (equal x_k = x_{k+1} give
+ *     y_k >= y_{k+1}, which pools), so the result does not depend on how ties
+ *     are ordered.
+ *   - Errors: argument errors are returned synchronously (WS_ERR_INVALID) and
+ *     nothing is enqueued.  Errors found on the device (a NaN/Inf input, a
+ *     bounded wait that gave up) are OR-ed into the context's status word and
+ *     reported by ws_get_status; outputs of that call are then unspecified.
+ */
+#ifndef WS_PROX_H
+#define WS_PROX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WS_OK = 0,
+    WS_ERR_INVALID = 1,   /* bad argument (null pointer, negative size, lambda < 0 or not finite, ...) */
+    WS_ERR_NONFINITE = 2, /* an input value was NaN or +-Inf (device-detected) */
+    WS_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    WS_ERR_NOMEM = 4,     /* device allocation failed (plan creation only) */
+    WS_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up (device-detected) */
+    WS_ERR_INTERNAL = 6   /* an internal consistency check failed (device-detected) */
+} ws_status;
+
+typedef enum { WS_F32 = 0, WS_F64 = 1 } ws_dtype;
+
+/* Arithmetic used for the cluster values.  Both modes take every merge
+ * decision exactly (128-bit fixed-point prefix sums, integer comparisons), so
+ * they produce the same partition; they differ in how a cluster mean and its
+ * shift are rounded:
+ *   WS_PREC_FP32_COMP: FP32 arithmetic on the exact integer cluster sum
+ *                      (error a few FP32 ulps of max|w| + lambda);
+ *   WS_PREC_FP64:      FP64 arithmetic (error a few FP64 ulps). */
+typedef enum { WS_PREC_FP32_COMP = 0, WS_PREC_FP64 = 1 } ws_prec;
+
+typedef struct ws_ctx ws_ctx;   /* device selection + asynchronous status word */
+typedef struct ws_plan ws_plan; /* segment layout + all scratch for one batch shape */
+
+/* Create a context on CUDA device `device` (allocates a few bytes of device
+ * memory for the status word).  Returns WS_OK and sets *ctx. */
+ws_status ws_ctx_create(ws_ctx** ctx, int device);
+void ws_ctx_destroy(ws_ctx* ctx);
+
+/* Plan a batch: `offsets` is a HOST array of n_seg + 1 non-decreasing int64
+ * with offsets[0] = 0; n = offsets[n_seg] values of type `dtype`.  Segments
+ * must be shorter than 2^31.  Allocates every buffer the calls need
+ * (synchronous; not capturable).  The plan copies the offsets; the caller may
+ * free them afterwards. */
+ws_status ws_plan_create(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg,
+                         ws_dtype dtype);
+void ws_plan_destroy(ws_plan* plan);
+
+/* Batched forward (Alg. 2 per segment, lambda = lambdas[s] from DEVICE memory,
+ * n_seg doubles, each >= 0 and finite -- checked on the device, reported as
+ * WS_ERR_INVALID through ws_get_status).  values/out: n elements of the
+ * plan's dtype; cluster_ids: n int32 (nullable); n_clusters: n_seg int64
+ * (nullable) receives the number of clusters of each segment. */
+ws_status ws_prox_batched(ws_plan* plan, const void* values, const double* lambdas, void* out,
+                          int32_t* cluster_ids, int64_t* n_clusters, ws_prec prec, void* stream);
+
+/* Single vector of length d with a host lambda.  Plans (and allocates) on
+ * first use of a given (d, dtype) and caches the plan in the context, so the
+ * first call for a shape is not capturable; later calls are.  n_clusters is
+ * a nullable DEVICE pointer to one int64. */
+ws_status ws_prox(ws_ctx* ctx, const void* w, int64_t d, double lambda, void* out,
+                  int32_t* cluster_ids, int64_t* n_clusters, ws_dtype dtype, ws_prec prec,
+                  void* stream);
+
+/* Backward of the forward with the partition held fixed (the Jacobian of the
+ * cluster means): grad_in[i] = mean of grad_out over the cluster of i, where
+ * clusters are given by (segment, cluster_ids[i]) as written by the forward on
+ * the same plan.  grad_out/grad_in: n elements of the plan's dtype, may alias. */
+ws_status ws_prox_backward_batched(ws_plan* plan, const void* grad_out, const int32_t* cluster_ids,
+                                   void* grad_in, void* stream);
+
+/* Single-vector backward (plan cached in the context as for ws_prox). */
+ws_status ws_prox_backward(ws_ctx* ctx, const void* grad_out, const int32_t* cluster_ids, int64_t d,
+                           void* grad_in, ws_dtype dtype, void* stream);
+
+/* Synchronise `stream`, then return and clear the context's device status
+ * word (WS_OK if no device-side error happened since the last call). */
+ws_status ws_get_status(ws_ctx* ctx, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* ws_status_string(ws_status s);
+
+/* Set the iteration bound of every device-side spin-wait (decoupled
+ * look-back).  A wait that exceeds it gives up, sets WS_ERR_TIMEOUT and lets
+ * its kernel exit.  0 restores the default.  Test hook. */
+void ws_debug_set_spin_limit(ws_ctx* ctx, int64_t limit);
+
+/* Segments no longer than `small_max` elements go to the fused single-CTA
+ * kernel, longer ones to the device-wide path.  Applies to plans created
+ * afterwards (cached single-vector plans are dropped); a negative value
+ * restores the default (4096 for float, 2048 for double, also the maximum).
+ * Test hook: lets small inputs exercise the device-wide path. */
+void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max);
+
+/* Runs only the radix sort of the device-wide path and writes, for every
+ * segment that the plan sends down that path, its values sorted ascending in
+ * IEEE total order (-0 before +0) at the segment's own position in
+ * `sorted_out` (device, plan dtype); other positions are left untouched.
+ * Test hook for bit-exact sort parity. */
+ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WS_PROX_H */

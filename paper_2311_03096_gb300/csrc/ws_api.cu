@@ -1,0 +1,453 @@
+// ws_api.cu -- the C ABI (include/ws_prox.h): contexts, plans and launches.
+// Host code only sequences launches; every step of the prox runs in the
+// kernels of ws_small.cu, ws_sort.cu and ws_large.cu.
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/ws_prox.h"
+#include "ws_kernels.cuh"
+
+namespace {
+
+constexpr uint64_t WS_DEFAULT_SPIN = 1ull << 24;
+
+struct PlanCacheEntry {
+    int64_t d;
+    ws_dtype dtype;
+    ws_plan* plan;
+};
+
+}  // namespace
+
+struct ws_ctx {
+    int device = 0;
+    uint32_t* status = nullptr;   // device status word
+    uint64_t spin_limit = WS_DEFAULT_SPIN;
+    int64_t small_max_override = -1;
+    std::vector<PlanCacheEntry> cache;
+    std::mutex mu;
+};
+
+struct ws_plan {
+    ws_ctx* ctx = nullptr;
+    ws_dtype dtype = WS_F32;
+    int64_t n = 0, n_seg = 0;
+    int64_t small_max = 0;
+    std::vector<int64_t> h_offsets;
+    int64_t* d_offsets = nullptr;
+    int32_t* d_small = nullptr;
+    int n_small = 0;
+    double* d_lambda1 = nullptr;   // lambda slot for single-vector calls
+    // large path
+    int n_lseg = 0, n_sort_tiles = 0, n_hull_tiles = 0;
+    int64_t n_keys = 0;
+    LargeSeg* d_lsegs = nullptr;
+    TileDesc* d_sort_tiles = nullptr;
+    TileDesc* d_hull_tiles = nullptr;
+    std::vector<MergeNode*> d_levels;
+    std::vector<int> level_counts;
+    MergeNode* d_nodes_all = nullptr;
+    std::vector<void*> allocs;
+    void* keys_a = nullptr;
+    void* keys_b = nullptr;
+    uint32_t* hist = nullptr;
+    uint64_t* lookback = nullptr;
+    uint32_t* tile_counter = nullptr;
+    uint16_t* vp = nullptr;
+    i128* vx = nullptr;
+    int32_t* nvert = nullptr;
+    i128* tile_total = nullptr;
+    i128* tile_offset = nullptr;
+    Piece* pieces = nullptr;
+    int32_t* npieces = nullptr;
+    int32_t* tile_piece = nullptr;
+    SegRuntime* rt = nullptr;
+    void* table = nullptr;
+    int32_t* dir = nullptr;
+    void* bsum = nullptr;
+    int32_t* bcnt = nullptr;
+};
+
+namespace {
+
+template <typename T>
+LargeWork<T> make_work(const ws_plan* p) {
+    typedef typename KeyOf<T>::K K;
+    LargeWork<T> W;
+    W.n_lseg = p->n_lseg;
+    W.n_sort_tiles = p->n_sort_tiles;
+    W.n_hull_tiles = p->n_hull_tiles;
+    W.n_keys = p->n_keys;
+    W.lsegs = p->d_lsegs;
+    W.sort_tiles = p->d_sort_tiles;
+    W.hull_tiles = p->d_hull_tiles;
+    W.keys_a = (K*)p->keys_a;
+    W.keys_b = (K*)p->keys_b;
+    W.hist = p->hist;
+    W.lookback = p->lookback;
+    W.tile_counter = p->tile_counter;
+    W.vp = p->vp;
+    W.vx = p->vx;
+    W.nvert = p->nvert;
+    W.tile_total = p->tile_total;
+    W.tile_offset = p->tile_offset;
+    W.pieces = p->pieces;
+    W.npieces = p->npieces;
+    W.tile_piece = p->tile_piece;
+    W.rt = p->rt;
+    W.table = (CEntry<T>*)p->table;
+    W.dir = p->dir;
+    W.bsum = (T*)p->bsum;
+    W.bcnt = p->bcnt;
+    return W;
+}
+
+ws_status plan_alloc(ws_plan* p, void** dst, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return WS_ERR_NOMEM;
+    }
+    p->allocs.push_back(ptr);
+    *dst = ptr;
+    return WS_OK;
+}
+
+template <typename X>
+ws_status plan_upload(ws_plan* p, X** dst, const std::vector<X>& src) {
+    ws_status s = plan_alloc(p, (void**)dst, sizeof(X) * src.size());
+    if (s) return s;
+    if (!src.empty() && cudaMemcpy(*dst, src.data(), sizeof(X) * src.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return WS_ERR_CUDA;
+    return WS_OK;
+}
+
+int ceil_log2(int64_t v) {
+    int k = 0;
+    while (((int64_t)1 << k) < v) ++k;
+    return k;
+}
+
+ws_status build_plan(ws_plan* p) {
+    const bool f64 = p->dtype == WS_F64;
+    const int64_t small_cap = f64 ? SmallCfg<double>::CAP : SmallCfg<float>::CAP;
+    p->small_max = p->ctx->small_max_override >= 0 ? std::min<int64_t>(p->ctx->small_max_override, small_cap)
+                                                     : small_cap;
+    const size_t vsize = f64 ? 8 : 4, ksize = vsize;
+    std::vector<int32_t> small;
+    std::vector<LargeSeg> lsegs;
+    std::vector<TileDesc> stiles, htiles;
+    int64_t kpos = 0, dir_pos = 0;
+    for (int64_t s = 0; s < p->n_seg; ++s) {
+        int64_t a = p->h_offsets[s], len = p->h_offsets[s + 1] - a;
+        if (len <= p->small_max || len <= 1) { small.push_back((int32_t)s); continue; }
+        LargeSeg ls;
+        memset(&ls, 0, sizeof ls);
+        ls.vpos = a; ls.kpos = kpos; ls.len = len; ls.seg = (int32_t)s;
+        int lseg = (int)lsegs.size();
+        ls.sort_first = (int32_t)stiles.size();
+        for (int64_t o = 0, i = 0; o < len; o += WS_SORT_TILE, ++i) {
+            TileDesc td;
+            td.kpos = kpos + o; td.vpos = a + o; td.len = (int32_t)std::min<int64_t>(WS_SORT_TILE, len - o);
+            td.lseg = lseg; td.first = ls.sort_first; td.tin = (int32_t)i;
+            stiles.push_back(td);
+        }
+        ls.sort_count = (int32_t)stiles.size() - ls.sort_first;
+        ls.hull_first = (int32_t)htiles.size();
+        for (int64_t o = 0, i = 0; o < len; o += WS_HULL_TILE, ++i) {
+            TileDesc td;
+            td.kpos = kpos + o; td.vpos = a + o; td.len = (int32_t)std::min<int64_t>(WS_HULL_TILE, len - o);
+            td.lseg = lseg; td.first = ls.hull_first; td.tin = (int32_t)i;
+            htiles.push_back(td);
+        }
+        ls.hull_count = (int32_t)htiles.size() - ls.hull_first;
+        ls.dir_cap_log2 = ceil_log2(len);
+        ls.dir_pos = dir_pos;
+        dir_pos += ((int64_t)1 << ls.dir_cap_log2) + 1;
+        kpos += len;
+        lsegs.push_back(ls);
+    }
+    p->n_small = (int)small.size();
+    p->n_lseg = (int)lsegs.size();
+    p->n_sort_tiles = (int)stiles.size();
+    p->n_hull_tiles = (int)htiles.size();
+    p->n_keys = kpos;
+    // merge tree levels (host-built node lists)
+    std::vector<std::vector<MergeNode>> levels;
+    for (int L = 1;; ++L) {
+        std::vector<MergeNode> nodes;
+        bool any = false;
+        for (int i = 0; i < p->n_lseg; ++i) {
+            const LargeSeg& ls = lsegs[i];
+            if (((int64_t)1 << (L - 1)) >= ls.hull_count) continue;
+            any = true;
+            for (int64_t j = 0; (j << L) < ls.hull_count; ++j) {
+                int64_t left = ls.hull_first + (j << L);
+                int64_t right = left + ((int64_t)1 << (L - 1));
+                if (right >= ls.hull_first + ls.hull_count) continue;
+                MergeNode nd;
+                nd.lseg = i; nd.left = (int32_t)left; nd.right = (int32_t)right; nd.pad = 0;
+                nodes.push_back(nd);
+            }
+        }
+        if (!any) break;
+        levels.push_back(nodes);
+    }
+    ws_status st;
+    std::vector<int64_t> offs(p->h_offsets);
+    if ((st = plan_upload(p, &p->d_offsets, offs))) return st;
+    if ((st = plan_upload(p, &p->d_small, small))) return st;
+    if ((st = plan_alloc(p, (void**)&p->d_lambda1, sizeof(double)))) return st;
+    if (p->n_lseg == 0) return WS_OK;
+    if ((st = plan_upload(p, &p->d_lsegs, lsegs))) return st;
+    if ((st = plan_upload(p, &p->d_sort_tiles, stiles))) return st;
+    if ((st = plan_upload(p, &p->d_hull_tiles, htiles))) return st;
+    std::vector<MergeNode> all;
+    for (auto& lv : levels) { p->level_counts.push_back((int)lv.size()); all.insert(all.end(), lv.begin(), lv.end()); }
+    if ((st = plan_upload(p, &p->d_nodes_all, all))) return st;
+    size_t o = 0;
+    for (auto& lv : levels) { p->d_levels.push_back(p->d_nodes_all + o); o += lv.size(); }
+    const int P = f64 ? 8 : 4;
+    const size_t nk = (size_t)p->n_keys, nh = (size_t)p->n_hull_tiles, slots = nk + (size_t)p->n_lseg;
+    if ((st = plan_alloc(p, &p->keys_a, ksize * nk))) return st;
+    if ((st = plan_alloc(p, &p->keys_b, ksize * nk))) return st;
+    if ((st = plan_alloc(p, (void**)&p->hist, sizeof(uint32_t) * p->n_lseg * P * 256))) return st;
+    if ((st = plan_alloc(p, (void**)&p->lookback, sizeof(uint64_t) * (size_t)P * p->n_sort_tiles * 256))) return st;
+    if ((st = plan_alloc(p, (void**)&p->tile_counter, sizeof(uint32_t) * P))) return st;
+    if ((st = plan_alloc(p, (void**)&p->vp, sizeof(uint16_t) * nh * (WS_HULL_TILE + 1)))) return st;
+    if ((st = plan_alloc(p, (void**)&p->vx, sizeof(i128) * nh * (WS_HULL_TILE + 1)))) return st;
+    if ((st = plan_alloc(p, (void**)&p->nvert, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->tile_total, sizeof(i128) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->tile_offset, sizeof(i128) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->pieces, sizeof(Piece) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->npieces, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->tile_piece, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->rt, sizeof(SegRuntime) * p->n_lseg))) return st;
+    if ((st = plan_alloc(p, &p->table, (f64 ? sizeof(CEntry<double>) : sizeof(CEntry<float>)) * slots))) return st;
+    if ((st = plan_alloc(p, (void**)&p->dir, sizeof(int32_t) * (size_t)dir_pos))) return st;
+    if ((st = plan_alloc(p, &p->bsum, vsize * slots))) return st;
+    if ((st = plan_alloc(p, (void**)&p->bcnt, sizeof(int32_t) * slots))) return st;
+    if (cudaMemset(p->rt, 0, sizeof(SegRuntime) * p->n_lseg) != cudaSuccess) return WS_ERR_CUDA;
+    return WS_OK;
+}
+
+__global__ void k_set_lambda(double* dst, double v) { *dst = v; }
+
+ws_status map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return WS_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? WS_ERR_NOMEM : WS_ERR_CUDA;
+}
+
+template <typename T>
+ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, void* out, int32_t* ids,
+                      int64_t* n_clusters, ws_prec prec, cudaStream_t st) {
+    const int fp64 = prec == WS_PREC_FP64 ? 1 : 0;
+    cudaError_t e = ws_launch_small<T>((const T*)values, p->d_offsets, p->d_small, p->n_small, lambdas, (T*)out, ids,
+                                       n_clusters, fp64, p->ctx->status, st);
+    if (e) return map_cuda(e);
+    if (p->n_lseg > 0) {
+        LargeWork<T> W = make_work<T>(p);
+        e = ws_large_prox<T>(W, (const T*)values, lambdas, (T*)out, ids, n_clusters, fp64, p->ctx->status,
+                             p->ctx->spin_limit, p->d_levels.data(), p->level_counts.data(),
+                             (int)p->level_counts.size(), st);
+        if (e) return map_cuda(e);
+    }
+    return WS_OK;
+}
+
+template <typename T>
+ws_status run_backward(ws_plan* p, const void* g, const int32_t* ids, void* gin, cudaStream_t st) {
+    cudaError_t e = ws_launch_small_backward<T>((const T*)g, ids, p->d_offsets, p->d_small, p->n_small, (T*)gin,
+                                                p->ctx->status, st);
+    if (e) return map_cuda(e);
+    if (p->n_lseg > 0) {
+        LargeWork<T> W = make_work<T>(p);
+        e = ws_large_backward<T>(W, (const T*)g, ids, (T*)gin, p->ctx->status, st);
+        if (e) return map_cuda(e);
+    }
+    return WS_OK;
+}
+
+ws_plan* cached_plan(ws_ctx* ctx, int64_t d, ws_dtype dtype, ws_status* st) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    for (auto& c : ctx->cache)
+        if (c.d == d && c.dtype == dtype) { *st = WS_OK; return c.plan; }
+    int64_t offs[2] = {0, d};
+    ws_plan* p = nullptr;
+    *st = ws_plan_create(ctx, &p, offs, 1, dtype);
+    if (*st) return nullptr;
+    if (ctx->cache.size() >= 8) {   // keep at most 8 cached shapes
+        ws_plan_destroy(ctx->cache.front().plan);
+        ctx->cache.erase(ctx->cache.begin());
+    }
+    ctx->cache.push_back({d, dtype, p});
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ws_status_string(ws_status s) {
+    switch (s) {
+        case WS_OK: return "ok";
+        case WS_ERR_INVALID: return "invalid argument";
+        case WS_ERR_NONFINITE: return "non-finite input value";
+        case WS_ERR_CUDA: return "CUDA runtime error";
+        case WS_ERR_NOMEM: return "device allocation failed";
+        case WS_ERR_TIMEOUT: return "device-side wait gave up";
+        case WS_ERR_INTERNAL: return "internal consistency check failed";
+    }
+    return "unknown status";
+}
+
+ws_status ws_ctx_create(ws_ctx** ctx, int device) {
+    if (!ctx) return WS_ERR_INVALID;
+    *ctx = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) { cudaGetLastError(); return WS_ERR_INVALID; }
+    if (cudaSetDevice(device) != cudaSuccess) return WS_ERR_CUDA;
+    ws_ctx* c = new (std::nothrow) ws_ctx();
+    if (!c) return WS_ERR_NOMEM;
+    c->device = device;
+    if (cudaMalloc(&c->status, sizeof(uint32_t)) != cudaSuccess) { delete c; cudaGetLastError(); return WS_ERR_NOMEM; }
+    if (cudaMemset(c->status, 0, sizeof(uint32_t)) != cudaSuccess) { cudaFree(c->status); delete c; return WS_ERR_CUDA; }
+    *ctx = c;
+    return WS_OK;
+}
+
+void ws_ctx_destroy(ws_ctx* ctx) {
+    if (!ctx) return;
+    for (auto& c : ctx->cache) ws_plan_destroy(c.plan);
+    ctx->cache.clear();
+    if (ctx->status) cudaFree(ctx->status);
+    delete ctx;
+}
+
+ws_status ws_plan_create(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype) {
+    if (!ctx || !plan || n_seg < 0 || (n_seg > 0 && !offsets) || (dtype != WS_F32 && dtype != WS_F64))
+        return WS_ERR_INVALID;
+    *plan = nullptr;
+    if (n_seg > 0 && offsets[0] != 0) return WS_ERR_INVALID;
+    if (n_seg >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    for (int64_t s = 0; s < n_seg; ++s) {
+        int64_t len = offsets[s + 1] - offsets[s];
+        if (len < 0 || len >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return WS_ERR_CUDA;
+    ws_plan* p = new (std::nothrow) ws_plan();
+    if (!p) return WS_ERR_NOMEM;
+    p->ctx = ctx;
+    p->dtype = dtype;
+    p->n_seg = n_seg;
+    p->h_offsets.assign(offsets ? offsets : nullptr, offsets ? offsets + n_seg + 1 : nullptr);
+    if (n_seg == 0) p->h_offsets.assign(1, 0);
+    p->n = p->h_offsets.back();
+    ws_status st = build_plan(p);
+    if (st) { ws_plan_destroy(p); return st; }
+    *plan = p;
+    return WS_OK;
+}
+
+void ws_plan_destroy(ws_plan* plan) {
+    if (!plan) return;
+    for (void* a : plan->allocs) cudaFree(a);
+    delete plan;
+}
+
+ws_status ws_prox_batched(ws_plan* plan, const void* values, const double* lambdas, void* out, int32_t* cluster_ids,
+                          int64_t* n_clusters, ws_prec prec, void* stream) {
+    if (!plan || (prec != WS_PREC_FP32_COMP && prec != WS_PREC_FP64)) return WS_ERR_INVALID;
+    if (plan->n > 0 && (!values || !out)) return WS_ERR_INVALID;
+    if (plan->n_seg > 0 && !lambdas) return WS_ERR_INVALID;
+    if (plan->n_seg == 0) return WS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->dtype == WS_F64 ? run_forward<double>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, st)
+                                 : run_forward<float>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, st);
+}
+
+ws_status ws_prox(ws_ctx* ctx, const void* w, int64_t d, double lambda, void* out, int32_t* cluster_ids,
+                  int64_t* n_clusters, ws_dtype dtype, ws_prec prec, void* stream) {
+    if (!ctx || d < 0 || !(lambda >= 0.0) || !(lambda <= 1.7976931348623157e308)) return WS_ERR_INVALID;
+    if (dtype != WS_F32 && dtype != WS_F64) return WS_ERR_INVALID;
+    if (d > 0 && (!w || !out)) return WS_ERR_INVALID;
+    if (d >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    ws_status st;
+    ws_plan* p = cached_plan(ctx, d, dtype, &st);
+    if (!p) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_set_lambda<<<1, 1, 0, s>>>(p->d_lambda1, lambda);
+    if (cudaGetLastError() != cudaSuccess) return WS_ERR_CUDA;
+    return ws_prox_batched(p, w, p->d_lambda1, out, cluster_ids, n_clusters, prec, stream);
+}
+
+ws_status ws_prox_backward_batched(ws_plan* plan, const void* grad_out, const int32_t* cluster_ids, void* grad_in,
+                                   void* stream) {
+    if (!plan) return WS_ERR_INVALID;
+    if (plan->n > 0 && (!grad_out || !cluster_ids || !grad_in)) return WS_ERR_INVALID;
+    if (plan->n_seg == 0) return WS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    return plan->dtype == WS_F64 ? run_backward<double>(plan, grad_out, cluster_ids, grad_in, st)
+                                 : run_backward<float>(plan, grad_out, cluster_ids, grad_in, st);
+}
+
+ws_status ws_prox_backward(ws_ctx* ctx, const void* grad_out, const int32_t* cluster_ids, int64_t d, void* grad_in,
+                           ws_dtype dtype, void* stream) {
+    if (!ctx || d < 0 || (dtype != WS_F32 && dtype != WS_F64)) return WS_ERR_INVALID;
+    if (d >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    ws_status st;
+    ws_plan* p = cached_plan(ctx, d, dtype, &st);
+    if (!p) return st;
+    return ws_prox_backward_batched(p, grad_out, cluster_ids, grad_in, stream);
+}
+
+ws_status ws_get_status(ws_ctx* ctx, void* stream) {
+    if (!ctx) return WS_ERR_INVALID;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) { cudaGetLastError(); return WS_ERR_CUDA; }
+    uint32_t h = 0;
+    if (cudaMemcpy(&h, ctx->status, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return WS_ERR_CUDA;
+    if (h && cudaMemset(ctx->status, 0, sizeof(uint32_t)) != cudaSuccess) return WS_ERR_CUDA;
+    if (h & WS_STATUS_NONFINITE) return WS_ERR_NONFINITE;
+    if (h & WS_STATUS_BAD_LAMBDA) return WS_ERR_INVALID;
+    if (h & WS_STATUS_TIMEOUT) return WS_ERR_TIMEOUT;
+    if (h & WS_STATUS_INTERNAL) return WS_ERR_INTERNAL;
+    return WS_OK;
+}
+
+void ws_debug_set_spin_limit(ws_ctx* ctx, int64_t limit) {
+    if (ctx) ctx->spin_limit = limit > 0 ? (uint64_t)limit : WS_DEFAULT_SPIN;
+}
+
+void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max) {
+    if (!ctx) return;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->small_max_override = small_max;
+    for (auto& c : ctx->cache) ws_plan_destroy(c.plan);
+    ctx->cache.clear();
+}
+
+ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, void* stream) {
+    if (!plan || (plan->n > 0 && (!values || !sorted_out))) return WS_ERR_INVALID;
+    if (plan->n_lseg == 0) return WS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (plan->dtype == WS_F64) {
+        LargeWork<double> W = make_work<double>(plan);
+        uint64_t* sorted = nullptr;
+        e = ws_large_sort<double>(W, (const double*)values, plan->ctx->status, plan->ctx->spin_limit, st, &sorted);
+        if (!e) e = ws_large_copy_sorted<double>(W, sorted, (double*)sorted_out, st);
+    } else {
+        LargeWork<float> W = make_work<float>(plan);
+        uint32_t* sorted = nullptr;
+        e = ws_large_sort<float>(W, (const float*)values, plan->ctx->status, plan->ctx->spin_limit, st, &sorted);
+        if (!e) e = ws_large_copy_sorted<float>(W, sorted, (float*)sorted_out, st);
+    }
+    return map_cuda(e);
+}
+
+}  // extern "C"

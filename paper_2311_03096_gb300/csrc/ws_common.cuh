@@ -1,0 +1,278 @@
+// ws_common.cuh -- shared device helpers of the GB300 prox_R path.
+//
+// Notation (arXiv 2311.03096): a segment of d weights is sorted ascending into
+// x_0..x_{d-1} (0-based here); the shift of Alg. 2 for sorted position j is
+// lambda*(d - 1 - 2j)/(d - 1) (the paper's lambda(d+1-2k)/(d-1) with k = j+1).
+// Points P_p = (p, S_p), p = 0..d, S_p = sum_{j<p} y_j: the isotonic
+// regression of y (Sec. 3) is the slope sequence of the lower convex hull of
+// these points, pooled on >= (Sec. 4.1).  Two facts make the hull exact and
+// cheap:
+//   * S_p = X_p + lambda p (d - p)/(d - 1) with X_p = sum_{j<p} x_j, so
+//     slope(a, b) = mean(x_a..x_{b-1}) + lambda (d - a - b)/(d - 1): the shift
+//     never has to be stored;
+//   * X is carried in 128-bit fixed point (q_j = x_j * 2^L, |q_j| <= 2^58,
+//     exact for every input whose values span < ~2^(58-24) of dynamic range),
+//     and the "is b a strict hull vertex between a and c" test is decided
+//     with exact integer arithmetic (below), so merge decisions never round.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+// ---------------------------------------------------------------------------
+// status bits OR-ed into the context's device status word
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+    WS_STATUS_NONFINITE = 1u,
+    WS_STATUS_TIMEOUT = 2u,
+    WS_STATUS_INTERNAL = 4u,
+    WS_STATUS_BAD_LAMBDA = 8u,
+};
+
+__device__ __forceinline__ void ws_flag(uint32_t* status, uint32_t bit) {
+    if (status) atomicOr(status, bit);
+}
+
+// ---------------------------------------------------------------------------
+// IEEE total-order keys (-0 < +0), as unsigned integers
+// ---------------------------------------------------------------------------
+template <typename T> struct KeyOf;
+template <> struct KeyOf<float> {
+    typedef uint32_t K;
+    static constexpr int BITS = 32;
+    static constexpr int MANT = 23;   // stored mantissa bits
+    static constexpr int EXPMASK = 0xff;
+    static constexpr int FIX_OFS = 34;   // 58 - (MANT + 1)
+    static constexpr int L_BASE = 184;   // L = L_BASE - emax  (150 + FIX_OFS)
+    __device__ __forceinline__ static K to_key(float v) {
+        uint32_t b = __float_as_uint(v);
+        return b ^ ((b >> 31) ? 0xffffffffu : 0x80000000u);
+    }
+    __device__ __forceinline__ static float from_key(K k) {
+        return __uint_as_float(k ^ ((k >> 31) ? 0x80000000u : 0xffffffffu));
+    }
+    __device__ __forceinline__ static uint32_t bits(float v) { return __float_as_uint(v); }
+};
+template <> struct KeyOf<double> {
+    typedef uint64_t K;
+    static constexpr int BITS = 64;
+    static constexpr int MANT = 52;
+    static constexpr int EXPMASK = 0x7ff;
+    static constexpr int FIX_OFS = 5;     // 58 - (MANT + 1)
+    static constexpr int L_BASE = 1080;   // 1075 + FIX_OFS
+    __device__ __forceinline__ static K to_key(double v) {
+        uint64_t b = (uint64_t)__double_as_longlong(v);
+        return b ^ ((b >> 63) ? 0xffffffffffffffffull : 0x8000000000000000ull);
+    }
+    __device__ __forceinline__ static double from_key(K k) {
+        return __longlong_as_double((long long)(k ^ ((k >> 63) ? 0x8000000000000000ull : 0xffffffffffffffffull)));
+    }
+    __device__ __forceinline__ static uint64_t bits(double v) { return (uint64_t)__double_as_longlong(v); }
+};
+
+template <typename T> __device__ __forceinline__ bool ws_isfinite(T v) {
+    typedef KeyOf<T> KO;
+    uint64_t b = (uint64_t)KO::bits(v);
+    int e = (int)((b >> KO::MANT) & KO::EXPMASK);
+    return e != KO::EXPMASK;
+}
+
+// Effective biased exponent (denormals count as exponent 1).
+template <typename T> __device__ __forceinline__ int ws_eff_exp(T v) {
+    typedef KeyOf<T> KO;
+    uint64_t b = (uint64_t)KO::bits(v);
+    int e = (int)((b >> KO::MANT) & KO::EXPMASK);
+    return e == 0 ? 1 : e;
+}
+
+// Fixed-point image q = x * 2^L, L = L_BASE - emax, truncated toward zero
+// when x has bits below 2^-L (monotone, so sorted order is preserved).
+// |q| <= 2^58 whenever the effective exponent of x is <= emax.
+template <typename T> __device__ __forceinline__ int64_t ws_fixed(T v, int emax) {
+    typedef KeyOf<T> KO;
+    uint64_t b = (uint64_t)KO::bits(v);
+    int e = (int)((b >> KO::MANT) & KO::EXPMASK);
+    uint64_t m = b & ((1ull << KO::MANT) - 1ull);
+    if (e == 0) e = 1; else m |= (1ull << KO::MANT);
+    int sh = e - emax + KO::FIX_OFS;
+    uint64_t mag;
+    if (sh >= 0) mag = m << sh;            // sh <= FIX_OFS, so m << sh < 2^58
+    else mag = (sh > -64) ? (m >> (-sh)) : 0ull;
+    bool neg = (b >> (KO::BITS - 1)) & 1ull;
+    return neg ? -(int64_t)mag : (int64_t)mag;
+}
+
+// ---------------------------------------------------------------------------
+// Per-segment constants of the exact hull test
+// ---------------------------------------------------------------------------
+struct SegConst {
+    int64_t d;        // segment length
+    int L;            // fixed-point scale: q = x * 2^L
+    int s;            // e_lambda + L  (lambda = mlam * 2^e_lambda exactly)
+    uint64_t mlam;    // integer mantissa of lambda (0 iff lambda == 0)
+    uint64_t dm1;     // d - 1 (>= 1 when used)
+    float mu_f;       // lambda / (d - 1) rounded to float
+    double mu_d;      // lambda / (d - 1) in double
+};
+
+// lambda = mlam * 2^elam exactly (lambda >= 0, finite).
+__device__ __forceinline__ void ws_split_lambda(double lam, uint64_t& mlam, int& elam) {
+    uint64_t b = (uint64_t)__double_as_longlong(lam);
+    int e = (int)((b >> 52) & 0x7ff);
+    uint64_t m = b & ((1ull << 52) - 1ull);
+    if (e == 0) e = 1; else m |= (1ull << 52);
+    mlam = m;
+    elam = e - 1075;
+    if (m == 0) elam = 0;
+}
+
+template <typename T>
+__device__ __forceinline__ SegConst ws_seg_const(int64_t d, double lam, int emax) {
+    SegConst c;
+    c.d = d;
+    c.L = KeyOf<T>::L_BASE - emax;
+    int elam;
+    ws_split_lambda(lam, c.mlam, elam);
+    c.s = elam + c.L;
+    c.dm1 = d > 1 ? (uint64_t)(d - 1) : 1ull;
+    c.mu_d = d > 1 ? lam / (double)(d - 1) : 0.0;
+    c.mu_f = (float)c.mu_d;
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// 192-bit unsigned helpers for the exact comparison
+// ---------------------------------------------------------------------------
+struct U192 { uint64_t w0, w1, w2; };   // value = w0 + w1 2^64 + w2 2^128
+
+__device__ __forceinline__ int ws_bitlen64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
+__device__ __forceinline__ int ws_bitlen128(u128 v) {
+    uint64_t hi = (uint64_t)(v >> 64);
+    return hi ? 64 + ws_bitlen64(hi) : ws_bitlen64((uint64_t)v);
+}
+__device__ __forceinline__ int ws_bitlen192(const U192& v) {
+    if (v.w2) return 128 + ws_bitlen64(v.w2);
+    if (v.w1) return 64 + ws_bitlen64(v.w1);
+    return ws_bitlen64(v.w0);
+}
+__device__ __forceinline__ U192 ws_mul128x64(u128 a, uint64_t b) {
+    u128 lo = (u128)(uint64_t)a * b;
+    u128 hi = (u128)(uint64_t)(a >> 64) * b;
+    U192 r;
+    r.w0 = (uint64_t)lo;
+    u128 mid = (lo >> 64) + (u128)(uint64_t)hi;
+    r.w1 = (uint64_t)mid;
+    r.w2 = (uint64_t)(mid >> 64) + (uint64_t)(hi >> 64);
+    return r;
+}
+__device__ __forceinline__ U192 ws_shl192(const U192& v, int k) {   // 0 <= k < 192
+    U192 r = v;
+    while (k >= 64) { r.w2 = r.w1; r.w1 = r.w0; r.w0 = 0; k -= 64; }
+    if (k > 0) {
+        r.w2 = (r.w2 << k) | (r.w1 >> (64 - k));
+        r.w1 = (r.w1 << k) | (r.w0 >> (64 - k));
+        r.w0 = r.w0 << k;
+    }
+    return r;
+}
+__device__ __forceinline__ int ws_cmp192(const U192& a, const U192& b) {
+    if (a.w2 != b.w2) return a.w2 > b.w2 ? 1 : -1;
+    if (a.w1 != b.w1) return a.w1 > b.w1 ? 1 : -1;
+    if (a.w0 != b.w0) return a.w0 > b.w0 ? 1 : -1;
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// The exact hull test.
+//   convex(a, b, c)  <=>  slope(a, b) < slope(b, c)  <=>  P_b is a strict
+//   vertex of the lower hull of {P_a, P_b, P_c}; pooling on >= means a point
+//   on the chord is NOT a vertex.
+// With A = X_b - X_a, B = X_c - X_b (fixed point), n1 = b - a, n2 = c - b:
+//   slope(b,c) - slope(a,b) = B/n2 - A/n1 - mu (c - a),   mu = lambda/(d-1)
+// so convex <=> (B n1 - A n2) (d - 1) > lambda 2^L (c - a) n1 n2, and with
+// lambda = mlam 2^elam every quantity is an integer: compare
+//   LHS = (B n1 - A n2) (d - 1)   vs   RHS = mlam (c - a) n1 n2 2^(elam + L).
+// Sorted x gives B n1 - A n2 >= 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool ws_convex(i128 Xa, i128 Xb, i128 Xc, int64_t a, int64_t b, int64_t c,
+                                          const SegConst& sc) {
+    i128 A = Xb - Xa, B = Xc - Xb;
+    uint64_t n1 = (uint64_t)(b - a), n2 = (uint64_t)(c - b);
+    i128 D = B * (i128)n1 - A * (i128)n2;
+    if (D <= 0) return false;
+    if (sc.mlam == 0) return true;
+    u128 Du = (u128)D;
+    u128 P = (u128)((uint64_t)(c - a) * n1) * (u128)n2;
+    int blD = ws_bitlen128(Du), blm = ws_bitlen64(sc.dm1);
+    int blP = ws_bitlen128(P), blL = ws_bitlen64(sc.mlam);
+    int lhs_lo = blD + blm - 1, lhs_hi = blD + blm;
+    int rhs_lo = blP + blL - 1 + sc.s, rhs_hi = blP + blL + sc.s;
+    if (lhs_lo > rhs_hi) return true;
+    if (lhs_hi < rhs_lo) return false;
+    U192 Lv = ws_mul128x64(Du, sc.dm1);
+    U192 Rv = ws_mul128x64(P, sc.mlam);
+    int bl = ws_bitlen192(Lv), brr = ws_bitlen192(Rv);
+    int br = brr + sc.s;
+    if (bl != br) return bl > br;
+    Lv = ws_shl192(Lv, 192 - bl);
+    Rv = ws_shl192(Rv, 192 - brr);
+    return ws_cmp192(Lv, Rv) > 0;
+}
+
+// ---------------------------------------------------------------------------
+// Cluster values.  A cluster covers sorted positions [a, b) with exact
+// fixed-point sum SX; its value is mean(x_a..x_{b-1}) + mu (d - a - b).
+// ---------------------------------------------------------------------------
+// v * 2^-neg_exp, rounded to float (high and low 64-bit halves converted
+// separately, so all significant bits take part in the rounding).
+__device__ __forceinline__ float ws_i128_to_float_scaled(i128 v, int neg_exp) {
+    // keep the top 62 significant bits (exact shift), then one rounding to float
+    u128 mag = v < 0 ? (u128)(-v) : (u128)v;
+    int sh = ws_bitlen128(mag) - 62;
+    if (sh < 0) sh = 0;
+    long long t = (long long)(v >> sh);
+    return ldexpf(__ll2float_rn(t), sh - neg_exp);
+}
+__device__ __forceinline__ double ws_i128_to_double(i128 v) {
+    long long hi = (long long)(v >> 64);
+    unsigned long long lo = (unsigned long long)(uint64_t)v;
+    return fma(__ll2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo));
+}
+
+template <typename T> struct ValueOut;
+template <> struct ValueOut<float> {
+    __device__ __forceinline__ static float value(i128 SX, int64_t a, int64_t b, float xsingle, const SegConst& sc,
+                                                  bool fp64) {
+        int64_t n = b - a;
+        int64_t t = sc.d - a - b;
+        if (fp64) {
+            double mean = (n == 1) ? (double)xsingle : ldexp(ws_i128_to_double(SX) / (double)n, -sc.L);
+            return (float)(mean + sc.mu_d * (double)t);
+        }
+        float mean = (n == 1) ? xsingle : ldexpf(ws_i128_to_float_scaled(SX, 0) / (float)n, -sc.L);
+        return mean + sc.mu_f * (float)t;
+    }
+};
+template <> struct ValueOut<double> {
+    __device__ __forceinline__ static double value(i128 SX, int64_t a, int64_t b, double xsingle,
+                                                   const SegConst& sc, bool fp64) {
+        int64_t n = b - a;
+        int64_t t = sc.d - a - b;
+        if (!fp64) {
+            // FP32 arithmetic on the exact sum, widened to the output type
+            float mean = (n == 1) ? (float)xsingle : ldexpf(ws_i128_to_float_scaled(SX, 0) / (float)n, -sc.L);
+            return (double)(mean + sc.mu_f * (float)t);
+        }
+        double mean = (n == 1) ? xsingle : ldexp(ws_i128_to_double(SX) / (double)n, -sc.L);
+        return mean + sc.mu_d * (double)t;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Bounded spin-wait helper: every device-side wait has an iteration limit.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ws_backoff(int it) {
+    if (it > 64) __nanosleep(it > 4096 ? 256 : 32);
+}

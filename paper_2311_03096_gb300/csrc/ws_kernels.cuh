@@ -1,0 +1,123 @@
+// ws_kernels.cuh -- launch interface between the C ABI (ws_api.cu) and the
+// kernels.  Internal; not installed.
+#pragma once
+#include "ws_block.cuh"
+
+template <typename T> struct SmallCfg;
+template <> struct SmallCfg<float> { static constexpr int M = 16; static constexpr int CAP = 256 * 16; };
+template <> struct SmallCfg<double> { static constexpr int M = 8; static constexpr int CAP = 256 * 8; };
+
+// Large-path tile geometry.
+constexpr int WS_SORT_NT = 512;              // threads per onesweep CTA
+constexpr int WS_SORT_ITEMS = 16;            // keys per thread
+constexpr int WS_SORT_TILE = WS_SORT_NT * WS_SORT_ITEMS;   // 8192 keys per sort tile
+constexpr int WS_HULL_NT = 256;              // threads per hull-tile CTA
+constexpr int WS_HULL_M = 16;                // points per thread chunk
+constexpr int WS_HULL_TILE = WS_HULL_NT * WS_HULL_M;       // 4096 elements per hull tile
+
+// One tile of a large segment (sort tiles and hull tiles use the same record).
+struct TileDesc {
+    int64_t kpos;      // first element in the compact key buffer
+    int64_t vpos;      // first element in the caller's value array
+    int32_t len;       // elements in the tile
+    int32_t lseg;      // large-segment index
+    int32_t first;     // global index of the segment's first tile (of this kind)
+    int32_t tin;       // index of the tile inside its segment
+};
+
+// One large segment.
+struct LargeSeg {
+    int64_t vpos;      // first element in the caller's arrays
+    int64_t kpos;      // first element in the compact key buffer
+    int64_t len;
+    int32_t seg;       // index in the caller's segment list
+    int32_t sort_first, sort_count;   // sort tiles
+    int32_t hull_first, hull_count;   // hull tiles
+    int64_t dir_pos;   // directory slice start
+    int32_t dir_cap_log2;             // directory slice holds 2^dir_cap_log2 + 1 entries
+    int32_t pad;
+};
+
+// Merge-tree node (hull-tile level): children are hull-tile ranges.
+struct MergeNode {
+    int32_t lseg;
+    int32_t left;      // global hull-tile index of the left child's first tile
+    int32_t right;     // global hull-tile index of the right child's first tile
+    int32_t pad;
+};
+
+// A piece of a node hull: vertices [lo, hi) of hull tile `tile`; cum = rank of
+// its first vertex within the node hull.
+struct Piece {
+    int32_t tile;
+    uint16_t lo, hi;
+    int32_t cum;
+    int32_t pad;
+};
+
+// Cluster table entry (sorted by key within a segment).
+template <typename T> struct CEntry;
+template <> struct CEntry<float> { uint32_t key; float val; };
+template <> struct CEntry<double> { uint64_t key; double val; };
+
+// Per-segment run-time values computed on the device.
+struct SegRuntime {
+    int64_t n_clusters;
+    int64_t table_pos;  // first cluster-table entry of the segment
+    int32_t emax;
+    int32_t dir_log2;   // directory holds 2^dir_log2 buckets (+1 sentinel)
+    float lo, scale;    // bucket map: floor((x - lo) * scale)
+};
+
+template <typename T>
+cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
+                            const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
+                            uint32_t* status, cudaStream_t st);
+template <typename T>
+cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64_t* offsets, const int32_t* seg_list,
+                                     int n_list, T* gin, uint32_t* status, cudaStream_t st);
+
+// Large path workspace pointers (all device).
+template <typename T>
+struct LargeWork {
+    typedef typename KeyOf<T>::K K;
+    int n_lseg, n_sort_tiles, n_hull_tiles;
+    int64_t n_keys;
+    const LargeSeg* lsegs;
+    const TileDesc* sort_tiles;
+    const TileDesc* hull_tiles;
+    K* keys_a;
+    K* keys_b;
+    uint32_t* hist;          // [n_lseg][passes][256]
+    uint64_t* lookback;      // [passes][n_sort_tiles][256]
+    uint32_t* tile_counter;  // [passes]
+    // hull
+    uint16_t* vp;            // [n_hull_tiles][WS_HULL_TILE + 1] vertex points (tile-local)
+    i128* vx;                // [n_hull_tiles][WS_HULL_TILE + 1] X at vertices (tile-local)
+    int32_t* nvert;          // [n_hull_tiles]
+    i128* tile_total;        // [n_hull_tiles]
+    i128* tile_offset;       // [n_hull_tiles] exclusive prefix inside the segment
+    Piece* pieces;           // [n_hull_tiles]
+    int32_t* npieces;        // [n_hull_tiles] pieces of the node whose first tile is this index
+    int32_t* tile_piece;     // [n_hull_tiles] piece index in the root list or -1
+    SegRuntime* rt;          // [n_lseg]
+    CEntry<T>* table;        // [n_keys + n_lseg]
+    int32_t* dir;            // directory slices
+    // backward
+    T* bsum;                 // [n_keys + n_lseg]
+    int32_t* bcnt;           // [n_keys + n_lseg]
+};
+
+template <typename T>
+cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* status, uint64_t spin_limit,
+                          cudaStream_t st, typename KeyOf<T>::K** sorted);
+template <typename T>
+cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* lambdas, T* out, int32_t* ids,
+                          int64_t* n_clusters, int fp64, uint32_t* status, uint64_t spin_limit,
+                          const MergeNode* const* level_nodes, const int* level_counts, int n_levels,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* ids, T* gin, uint32_t* status,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t ws_large_copy_sorted(const LargeWork<T>& W, const typename KeyOf<T>::K* sorted, T* dst, cudaStream_t st);

@@ -1,0 +1,240 @@
+// ws_small.cu -- fused single-CTA prox for short segments (n <= 4096 for
+// float, 2048 for double): one CTA loads a segment once, sorts (key, index)
+// pairs in shared memory, builds the exact hull, and writes values and cluster
+// ids straight to their original positions.  HBM traffic is the I/O floor:
+// read w, write out and id (12 B/element for float).
+#include "ws_kernels.cuh"
+
+namespace {
+
+template <typename T, int NT, int M>
+struct SmallSmem {
+    typedef typename KeyOf<T>::K K;
+    static constexpr int CAP = NT * M;
+    K keys[CAP];
+    uint16_t idx[CAP];
+    int64_t loc[CAP + 1];   // prefix of q inside the point's chunk
+    i128 base[NT + 1];      // prefix of q at each chunk start
+    HullSmem<NT, M> hull;
+    uint16_t V[CAP + 1];    // hull vertices (points)
+    union {
+        struct {
+            uint32_t whist[(NT / 32) * 256];
+            uint32_t dcount[256], dstart[256];
+        } sort;
+        struct {
+            T val[CAP];
+            uint8_t mark[CAP];
+        } out;
+    } u;
+    i128 wsum128[NT / 32];
+    int wsum_i[NT / 32];
+    int flags;
+};
+
+template <typename T, int NT, int M>
+__global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, const int64_t* __restrict__ offsets,
+                                              const int32_t* __restrict__ seg_list, const double* __restrict__ lambdas,
+                                              T* out, int32_t* ids, int64_t* n_clusters, int fp64,
+                                              uint32_t* status) {
+    typedef KeyOf<T> KO;
+    typedef typename KO::K K;
+    typedef SmallSmem<T, NT, M> S;
+    constexpr int CAP = S::CAP;
+    constexpr int ITEMS = M;   // items per thread in the sort
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S& s = *reinterpret_cast<S*>(smem_raw);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+
+    const int seg = seg_list[blockIdx.x];
+    const int64_t a0 = offsets[seg];
+    const int n = (int)(offsets[seg + 1] - a0);
+    const double lam = lambdas[seg];
+    if (!(lam >= 0.0) || !(lam <= 1.7976931348623157e308)) {
+        if (t == 0) ws_flag(status, WS_STATUS_BAD_LAMBDA);
+        return;
+    }
+    if (n <= 0 || n > CAP) {
+        if (n > CAP && t == 0) ws_flag(status, WS_STATUS_INTERNAL);
+        if (n == 0 && t == 0 && n_clusters) n_clusters[seg] = 0;
+        return;
+    }
+
+    // ---- load (striped per warp, coalesced), map to keys, check finiteness
+    if (t == 0) s.flags = 0;
+    __syncthreads();
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        int p = w * 32 * ITEMS + k * 32 + lane;
+        if (p < n) {
+            T v = values[a0 + p];
+            bad |= !ws_isfinite(v);
+            s.keys[p] = KO::to_key(v);
+            s.idx[p] = (uint16_t)p;
+        }
+    }
+    if (bad) atomicOr(&s.flags, 1);
+    __syncthreads();
+    if (s.flags) {
+        if (t == 0) ws_flag(status, WS_STATUS_NONFINITE);
+        return;
+    }
+    if (n == 1) {
+        if (t == 0) {
+            out[a0] = values[a0];
+            if (ids) ids[a0] = 0;
+            if (n_clusters) n_clusters[seg] = 1;
+        }
+        return;
+    }
+
+    // ---- LSD radix sort of (key, idx) in shared memory, 8-bit digits
+    for (int pass = 0; pass < KO::BITS / 8; ++pass) {
+        K kk[ITEMS];
+        uint16_t ii[ITEMS];
+        uint32_t dg[ITEMS];
+        bool valid[ITEMS];
+        int pos[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            int p = w * 32 * ITEMS + k * 32 + lane;
+            valid[k] = p < n;
+            kk[k] = valid[k] ? s.keys[p] : (K)0;
+            ii[k] = valid[k] ? s.idx[p] : (uint16_t)0;
+            dg[k] = (uint32_t)((kk[k] >> (8 * pass)) & 0xff);
+        }
+        __syncthreads();
+        ws_rank_digits<NT, ITEMS>(dg, valid, pos, s.u.sort.whist, s.u.sort.dcount, s.u.sort.dstart, nullptr);
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k)
+            if (valid[k]) { s.keys[pos[k]] = kk[k]; s.idx[pos[k]] = ii[k]; }
+        __syncthreads();
+    }
+
+    // ---- fixed point and prefix sums (blocked: thread t owns sorted [t*M, t*M+M))
+    const T xlo = KO::from_key(s.keys[0]), xhi = KO::from_key(s.keys[n - 1]);
+    const int emax = max(ws_eff_exp(xlo), ws_eff_exp(xhi));
+    const SegConst sc = ws_seg_const<T>(n, lam, emax);
+    i128 csum = 0;
+    {
+        int first = t * M;
+        int64_t run = 0;
+        for (int i = 0; i < M; ++i) {
+            int p = first + i;
+            if (p <= n) s.loc[p] = run;
+            if (p < n) run += ws_fixed<T>(KO::from_key(s.keys[p]), emax);
+        }
+        csum = (i128)run;
+    }
+    i128 total;
+    i128 ex = ws_block_excl_scan<NT, i128>(csum, s.wsum128, &total);
+    s.base[t] = ex;
+    if (t == 0) { s.base[NT] = total; if (n == CAP) s.loc[CAP] = 0; }
+    __syncthreads();
+    auto X = [&](int p) -> i128 { return s.base[p / M] + (i128)s.loc[p]; };
+
+    // ---- exact hull (in-CTA merge)
+    int nv;
+    ws_cta_hull<NT, M>(s.hull, n, X, sc, &nv);
+    {
+        int l = s.hull.lo[t], h = s.hull.hi[t], o = s.hull.cum[t];
+        for (int i = l; i < h; ++i) s.V[o + (i - l)] = s.hull.H[t * (M + 1) + i];
+    }
+    for (int p = t; p < n; p += NT) s.u.out.mark[p] = 0;
+    __syncthreads();
+    const int c = nv - 1;
+    if (s.V[0] != 0 || s.V[c] != n) { if (t == 0) ws_flag(status, WS_STATUS_INTERNAL); }
+
+    // ---- cluster values
+    for (int r = t; r < c; r += NT) {
+        int a = s.V[r], b = s.V[r + 1];
+        T xs = KO::from_key(s.keys[a]);
+        s.u.out.val[r] = ValueOut<T>::value(X(b) - X(a), a, b, xs, sc, fp64 != 0);
+        s.u.out.mark[a] = 1;
+    }
+    __syncthreads();
+
+    // ---- cluster id of every sorted position, then scatter to the original order
+    int cntm = 0;
+    for (int i = 0; i < M; ++i) { int p = t * M + i; if (p < n) cntm += s.u.out.mark[p]; }
+    int tot;
+    int run = ws_block_excl_scan<NT, int>(cntm, s.wsum_i, &tot);
+    for (int i = 0; i < M; ++i) {
+        int p = t * M + i;
+        if (p < n) {
+            run += s.u.out.mark[p];
+            int r = run - 1;
+            int64_t o = a0 + s.idx[p];
+            out[o] = s.u.out.val[r];
+            if (ids) ids[o] = r;
+        }
+    }
+    if (t == 0 && n_clusters) n_clusters[seg] = c;
+}
+
+// Backward for short segments: per-cluster mean of grad_out (shared-memory sums).
+template <typename T, int NT, int CAP>
+__global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, const int32_t* __restrict__ ids,
+                                                       const int64_t* __restrict__ offsets,
+                                                       const int32_t* __restrict__ seg_list, T* gin,
+                                                       uint32_t* status) {
+    __shared__ T sum[CAP];
+    __shared__ int cnt[CAP];
+    const int seg = seg_list[blockIdx.x];
+    const int64_t a0 = offsets[seg];
+    const int n = (int)(offsets[seg + 1] - a0);
+    if (n <= 0) return;
+    if (n > CAP) { if (threadIdx.x == 0) ws_flag(status, WS_STATUS_INTERNAL); return; }
+    for (int i = threadIdx.x; i < n; i += NT) { sum[i] = (T)0; cnt[i] = 0; }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += NT) {
+        int id = ids[a0 + i];
+        if (id < 0 || id >= n) { ws_flag(status, WS_STATUS_INTERNAL); continue; }
+        atomicAdd(&sum[id], g[a0 + i]);
+        atomicAdd(&cnt[id], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += NT) {
+        int id = ids[a0 + i];
+        if (id >= 0 && id < n) gin[a0 + i] = sum[id] / (T)cnt[id];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
+                            const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
+                            uint32_t* status, cudaStream_t st) {
+    constexpr int NT = 256;
+    constexpr int M = SmallCfg<T>::M;
+    if (n_list <= 0) return cudaSuccess;
+    size_t smem = sizeof(SmallSmem<T, NT, M>);
+    auto kern = k_small<T, NT, M>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<n_list, NT, smem, st>>>(values, offsets, seg_list, lambdas, out, ids, n_clusters, fp64, status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64_t* offsets, const int32_t* seg_list,
+                                     int n_list, T* gin, uint32_t* status, cudaStream_t st) {
+    constexpr int NT = 256;
+    if (n_list <= 0) return cudaSuccess;
+    k_small_backward<T, NT, SmallCfg<T>::CAP><<<n_list, NT, 0, st>>>(g, ids, offsets, seg_list, gin, status);
+    return cudaGetLastError();
+}
+
+template cudaError_t ws_launch_small<float>(const float*, const int64_t*, const int32_t*, int, const double*, float*,
+                                            int32_t*, int64_t*, int, uint32_t*, cudaStream_t);
+template cudaError_t ws_launch_small<double>(const double*, const int64_t*, const int32_t*, int, const double*,
+                                             double*, int32_t*, int64_t*, int, uint32_t*, cudaStream_t);
+template cudaError_t ws_launch_small_backward<float>(const float*, const int32_t*, const int64_t*, const int32_t*,
+                                                     int, float*, uint32_t*, cudaStream_t);
+template cudaError_t ws_launch_small_backward<double>(const double*, const int32_t*, const int64_t*,
+                                                      const int32_t*, int, double*, uint32_t*, cudaStream_t);

@@ -1,0 +1,219 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every input is seeded and synthetic (paper_2311_03096_gb300.inputs).  Sizes
+are chosen so the oracle finishes in seconds while the GPU path still spans
+several tiles and a ragged tail; the device-wide path is also forced onto
+small inputs with ws_debug_set_small_max.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2311_03096_gb300 import inputs  # noqa: E402
+from parity import compare_segment  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {("f64", "fp64"): 1e-12, ("f64", "fp32comp"): 1e-5, ("f32", "fp64"): 1e-5, ("f32", "fp32comp"): 1e-5}
+NP = {"f32": np.float32, "f64": np.float64}
+TT = {"f32": torch.float32, "f64": torch.float64}
+
+
+@pytest.fixture(scope="module")
+def ws():
+    from paper_2311_03096_gb300 import ws as _ws
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return _ws
+
+
+@pytest.fixture()
+def ctx(ws):
+    c = ws.Context.get(0)
+    c.set_small_max(-1)
+    c.set_spin_limit(0)
+    c.status()
+    yield c
+    c.set_small_max(-1)
+    c.set_spin_limit(0)
+
+
+def run_one(ws, ctx, w_np, lam, dt, prec):
+    w = torch.from_numpy(w_np).cuda()
+    out, ids, nc = ws.prox(w, lam, prec)
+    ctx.check(what="prox")
+    return out.cpu().numpy(), ids.cpu().numpy(), int(nc.item())
+
+
+# -- config: plain FP64 prox, d = 4096, lambda in {0, 0.1, 1, 1000} (single-CTA path)
+@pytest.mark.parametrize("lam", [0.0, 0.1, 1.0, 1000.0])
+@pytest.mark.parametrize("prec", ["fp64", "fp32comp"])
+def test_d4096_fp64(ws, ctx, lam, prec):
+    w_np = inputs.normal(4096, seed=0, dtype=np.float64)
+    out, ids, nc = run_one(ws, ctx, w_np, lam, "f64", prec)
+    compare_segment(w_np, lam, out, ids, nc, TOL[("f64", prec)])
+    if lam == 0.0 and prec == "fp64":
+        assert np.array_equal(out, w_np)   # identity, bit for bit
+    if lam == 1000.0:
+        assert nc == 1
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("d", [0, 1, 2, 3, 31, 32, 33, 255, 1000, 2047, 2048, 4095, 4096])
+def test_small_sizes(ws, ctx, dt, d):
+    w_np = inputs.normal_with_duplicates(d, seed=d + 17, dtype=NP[dt])
+    for lam in (0.0, 0.05, 2.0):
+        for prec in ("fp32comp", "fp64"):
+            out, ids, nc = run_one(ws, ctx, w_np, lam, dt, prec)
+            compare_segment(w_np, lam, out, ids, nc, TOL[(dt, prec)])
+
+
+def test_ties_and_signed_zero(ws, ctx):
+    w_np = np.array([0.0, -0.0, 1.0, 1.0, -1.0, 0.0, -0.0, 1.0], np.float32)
+    for lam in (0.0, 0.01, 1.0):
+        out, ids, nc = run_one(ws, ctx, w_np, lam, "f32", "fp64")
+        compare_segment(w_np, lam, out, ids, nc, 1e-6)
+
+
+@pytest.mark.parametrize("small_max", [0, 64, 1000])
+@pytest.mark.parametrize("d", [2, 3, 100, 4096, 4097, 9000, 20000])
+def test_device_wide_path_forced(ws, ctx, small_max, d):
+    ctx.set_small_max(small_max)
+    w_np = inputs.normal_with_duplicates(d, seed=d, dtype=np.float32)
+    for lam in (0.0, 1e-3, 0.3, 50.0):
+        out, ids, nc = run_one(ws, ctx, w_np, lam, "f32", "fp64")
+        compare_segment(w_np, lam, out, ids, nc, 1e-5)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("d", [5000, 70000, 2 ** 20 + 3])
+def test_device_wide_path(ws, ctx, dt, d):
+    w_np = inputs.normal_with_duplicates(d, seed=d, dtype=NP[dt])
+    for lam in (1e-2, 1.0, 1e2):
+        ref = oracle.prox(w_np, lam, return_perm=True)
+        for prec in ("fp32comp", "fp64"):
+            out, ids, nc = run_one(ws, ctx, w_np, lam, dt, prec)
+            compare_segment(w_np, lam, out, ids, nc, TOL[(dt, prec)], ref=ref)
+
+
+@pytest.mark.parametrize("d", [2 ** 12, 2 ** 16, 2 ** 20])
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_cascade(ws, ctx, d, shuffle):
+    w_np, lam = inputs.cascade(d, seed=1, shuffle=shuffle)
+    out, ids, nc = run_one(ws, ctx, w_np, lam, "f32", "fp64")
+    compare_segment(w_np, lam, out, ids, nc, 1e-5)
+    assert nc == 1
+
+
+@pytest.mark.parametrize("d", [2 ** 12, 2 ** 16, 2 ** 20])
+def test_mirror(ws, ctx, d):
+    w_np, lam = inputs.mirror(d, seed=2, shuffle=True)
+    out, ids, nc = run_one(ws, ctx, w_np, lam, "f32", "fp64")
+    compare_segment(w_np, lam, out, ids, nc, 1e-5)
+    assert nc == d // 2
+
+
+def test_debug_sort_bit_exact(ws, ctx):
+    ctx.set_small_max(0)
+    for dt in ("f32", "f64"):
+        for d in (3, 8192, 8193, 50000):
+            w_np = inputs.normal_with_duplicates(d, seed=d, dtype=NP[dt])
+            w_np[:5] = np.array([0.0, -0.0, 0.0, -0.0, 1.0], NP[dt])[: min(5, d)]
+            plan = ws.Plan([0, d], TT[dt])
+            w = torch.from_numpy(w_np).cuda()
+            s = torch.zeros_like(w)
+            plan.debug_sort(w, s)
+            ctx.check(what="debug_sort")
+            _, xs = oracle.sort(w_np)
+            got = s.cpu().numpy()
+            # bit-exact, including the sign of zeros
+            assert np.array_equal(got.view(np.uint32 if dt == "f32" else np.uint64),
+                                  xs.astype(NP[dt]).view(np.uint32 if dt == "f32" else np.uint64))
+
+
+def _batched_case(seed, n_seg=40, maxlen=30000):
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(0, maxlen, n_seg)
+    lens[:6] = [0, 1, 2, 4096, 4097, 8193]
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    vals = inputs.normal_with_duplicates(int(off[-1]), seed=seed, dtype=np.float32)
+    lam = np.exp(rng.uniform(np.log(1e-3), np.log(10.0), n_seg))
+    return vals, off, lam
+
+
+@pytest.mark.parametrize("prec", ["fp32comp", "fp64"])
+def test_batched(ws, ctx, prec):
+    vals, off, lam = _batched_case(3)
+    plan = ws.Plan(off, torch.float32)
+    out, ids, nc = plan.forward(torch.from_numpy(vals).cuda(), torch.from_numpy(lam).cuda(), prec)
+    ctx.check(what="batched")
+    out, ids, nc = out.cpu().numpy(), ids.cpu().numpy(), nc.cpu().numpy()
+    for s in range(len(lam)):
+        a, b = off[s], off[s + 1]
+        compare_segment(vals[a:b], lam[s], out[a:b], ids[a:b], nc[s], 1e-5)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+def test_backward_matches_oracle(ws, ctx, dt):
+    vals, off, lam = _batched_case(4, n_seg=12)
+    vals = vals.astype(NP[dt])
+    plan = ws.Plan(off, TT[dt])
+    out, ids, nc = plan.forward(torch.from_numpy(vals).cuda(), torch.from_numpy(lam).cuda(), "fp64")
+    g = inputs.normal(vals.shape[0], seed=9, dtype=NP[dt])
+    gin = plan.backward(torch.from_numpy(g).cuda(), ids)
+    ctx.check(what="backward")
+    ref = oracle.backward(g, ids.cpu().numpy(), off)
+    tol = 1e-12 if dt == "f64" else 1e-5
+    np.testing.assert_allclose(gin.cpu().numpy(), ref, atol=tol * (1 + np.abs(g).max()))
+
+
+def test_nonfinite_reported(ws, ctx):
+    for d in (100, 20000):
+        w_np = inputs.normal(d, seed=1, dtype=np.float32)
+        w_np[d // 2] = np.nan
+        w = torch.from_numpy(w_np).cuda()
+        ws.prox(w, 0.1)
+        assert ctx.status() == ws.WS_ERR_NONFINITE
+        w_np[d // 2] = np.inf
+        ws.prox(torch.from_numpy(w_np).cuda(), 0.1)
+        assert ctx.status() == ws.WS_ERR_NONFINITE
+    # the context stays usable
+    w_np = inputs.normal(1000, seed=2, dtype=np.float32)
+    out, ids, nc = run_one(ws, ctx, w_np, 0.1, "f32", "fp64")
+    compare_segment(w_np, 0.1, out, ids, nc, 1e-5)
+
+
+def test_invalid_arguments(ws, ctx):
+    w = torch.zeros(10, device="cuda")
+    with pytest.raises(ws.WSError):
+        ws.prox(w, -1.0)
+    with pytest.raises(ws.WSError):
+        ws.prox(w, float("nan"))
+    with pytest.raises(ws.WSError):
+        ws.Plan([1, 5])
+    plan = ws.Plan([0, 5, 10])
+    bad = torch.tensor([0.1, -0.5], dtype=torch.float64, device="cuda")
+    plan.forward(w, bad)
+    assert ctx.status() == ws.WS_ERR_INVALID
+
+
+def test_spin_wait_gives_up(ws, ctx):
+    """A look-back wait with a tiny bound gives up, reports WS_ERR_TIMEOUT and
+    the kernel exits; the context stays usable."""
+    ctx.set_spin_limit(1)
+    w_np = inputs.normal(2 ** 22, seed=3, dtype=np.float32)
+    w = torch.from_numpy(w_np).cuda()
+    st = ws.WS_OK
+    for _ in range(5):
+        ws.prox(w, 0.5)
+        st = ctx.status()
+        if st == ws.WS_ERR_TIMEOUT:
+            break
+        assert st == ws.WS_OK
+    assert st == ws.WS_ERR_TIMEOUT
+    ctx.set_spin_limit(0)
+    w_np = inputs.normal(20000, seed=4, dtype=np.float32)
+    out, ids, nc = run_one(ws, ctx, w_np, 0.5, "f32", "fp64")
+    compare_segment(w_np, 0.5, out, ids, nc, 1e-5)
