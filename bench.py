@@ -1,0 +1,395 @@
+"""Benchmark of prox_{lambda R} on GB300: one JSON line on stdout.
+
+Workload (the single-large-vector configuration): d = 2^26 FP32 weights,
+w_i ~ N(0, 1) with 10% of positions overwritten by exact duplicates, seeded;
+each step is one prox (the whole hot path: sort, shift, exact merge, cluster
+values, lookup back to the caller's order) with lambda cycling through
+{1e-2, 1, 1e2}.  The input (256 MiB) is larger than L2 and resident in HBM
+before the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica (the single-vector
+path does not shard), value = all ranks' elements / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores instead (rank 0
+only), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "prox_R elements/s and HBM-roofline fraction, FP32-comp vs FP64 at stated error"
+LAMBDAS = (1e-2, 1.0, 1e2)
+WORKLOAD = "single vector d=2^26 FP32 N(0,1) + 10% exact duplicates, lambda cycling {1e-2, 1, 1e2}"
+
+# Algorithmic HBM bytes per element for each kernel kind of the device-wide
+# path (FP32 storage; documented with the roofline in the design doc).
+ALGO_BYTES_PER_ELEM_F32 = {
+    "onesweep": 8,    # read key (pass 0: the value) + write key
+    "hist": 4,        # read the value
+    "tile_hull": 4,   # read the sorted key (hull vertices are data dependent, not counted)
+    "lookup": 12,     # read w, write out and cluster id (I/O floor)
+}
+
+# DRAM traffic per launch from one ncu capture (profiles/*.txt) and the hash of
+# the kernel sources it was taken on; reported as null once the sources change.
+NCU_TRAFFIC = {}
+NCU_SOURCE_HASH = None
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2311_03096_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) during the benchmark; lines are timestamped."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        inwin = [p for (t, p) in self.samples if t0 - 0.25 <= t <= t1 + 0.25]
+        use = inwin if len(inwin) >= 1 else [p for (_, p) in self.samples]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(p[2]) for p in use if num(p[2]) is not None]
+        mx = [num(p[3]) for p in use if num(p[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in use for i in range(4) if "Active" in p[6 + i] and "Not" not in p[6 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(use), "in_window": len(inwin)}
+
+
+def oracle_rate(w_sample: np.ndarray, steps: int):
+    """Time the FP64 oracle on a sample, cycling lambda; returns elements/s."""
+    import oracle
+
+    t = time.perf_counter()
+    for k in range(steps):
+        oracle.prox(w_sample, LAMBDAS[k % len(LAMBDAS)])
+    dt = time.perf_counter() - t
+    return w_sample.shape[0] * steps / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2311_03096_gb300 import inputs
+
+    oracle.build()
+    w = inputs.normal_with_duplicates(args.d, seed=args.seed, dtype=np.float32)
+    # size the per-step sample so that warmup + steps finish in about two minutes
+    probe = w[: 1 << 16]
+    rate, _ = oracle_rate(probe, 3)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n = int(min(args.d, max(1 << 14, 2 ** int(np.log2(max(1.0, rate * budget))))))
+    sample = w[:n]
+    for k in range(args.warmup):
+        oracle.prox(sample, LAMBDAS[k % 3])
+    value, dt = oracle_rate(sample, args.steps)
+    cfg = config_dict(args, world)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg,
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} elements of the workload vector per step (lambda cycling)"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, world):
+    return {"workload": WORKLOAD, "d": args.d, "lambdas": list(LAMBDAS), "storage": "f32", "prec": args.prec,
+            "seed": args.seed, "l2": "inputs larger than L2 (256 MiB vector per step)",
+            "parallelism": f"replicas x{world}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--d", type=int, default=1 << 26)
+    ap.add_argument("--prec", default="fp32comp", choices=["fp32comp", "fp64"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    import __graft_entry__
+    from paper_2311_03096_gb300 import inputs, ws
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = ws.Context.get(local)
+    stream = torch.cuda.current_stream()
+
+    w_np = inputs.normal_with_duplicates(args.d, seed=args.seed, dtype=np.float32)
+    w = torch.from_numpy(w_np).to(dev)
+    out = torch.empty_like(w)
+    ids = torch.empty(args.d, dtype=torch.int32, device=dev)
+    nc = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    # first call plans (allocates) and is excluded from everything below
+    ws.prox(w, 1.0, args.prec, ctx=ctx, out=out, n_clusters=nc)
+    ctx.check(what="bench warm-up")
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    time.sleep(0.5)
+    for k in range(args.warmup):
+        ws.prox(w, LAMBDAS[k % 3], args.prec, ctx=ctx, out=out, n_clusters=nc)
+    torch.cuda.synchronize()
+    ctx.check(what="bench warm-up")
+
+    # ---- timed region: K steps, inputs resident in HBM
+    ctx.profile(True)
+    launches0 = ctx.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    e0.record(stream)
+    for k in range(args.steps):
+        ws.prox(w, LAMBDAS[k % 3], args.prec, ctx=ctx, out=out, n_clusters=nc)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = ctx.launch_count() - launches0
+    ms_total = e0.elapsed_time(e1)
+    kern = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check(what="bench timed region")
+    ms_max = ms_total
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = args.d * args.steps * world / (ms_max / 1e3)
+    ms_per_step = ms_max / args.steps
+
+    # ---- dominant kernel roofline (live CUDA-event durations from the timed region)
+    peak, peak_kind = load_peaks()
+    shares = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / ms_total} for k, v in kern.items()}
+    dom = max(kern.items(), key=lambda kv: kv[1][0])[0] if kern else None
+    roofline = None
+    if dom is not None:
+        ms_avg = kern[dom][0] / kern[dom][1]
+        per_launch = ALGO_BYTES_PER_ELEM_F32.get(dom)
+        traffic = NCU_TRAFFIC.get(dom) if NCU_SOURCE_HASH == source_hash() else None
+        if per_launch is not None:
+            achieved = per_launch * args.d / (ms_avg / 1e3) / 1e9
+            roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                        "bytes_per_launch": per_launch * args.d, "ms_per_launch": ms_avg, "traffic": traffic}
+        else:
+            roofline = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                        "ms_per_launch": ms_avg, "traffic": traffic}
+
+    # ---- end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        h_w = torch.from_numpy(w_np).pin_memory()
+        h_out = torch.empty(args.d, dtype=torch.float32).pin_memory()
+        h_ids = torch.empty(args.d, dtype=torch.int32).pin_memory()
+        d_w = torch.empty_like(w)
+        n_e2e = max(3, min(args.steps, 50))
+        for k in range(2):
+            d_w.copy_(h_w, non_blocking=True)
+            o, i, _ = ws.prox(d_w, LAMBDAS[k % 3], args.prec, ctx=ctx, out=out, n_clusters=nc)
+            h_out.copy_(o, non_blocking=True)
+            h_ids.copy_(i, non_blocking=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(n_e2e):
+            d_w.copy_(h_w, non_blocking=True)
+            o, i, _ = ws.prox(d_w, LAMBDAS[k % 3], args.prec, ctx=ctx, out=out, n_clusters=nc)
+            h_out.copy_(o, non_blocking=True)
+            h_ids.copy_(i, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = f0.elapsed_time(f1)
+        if world > 1:
+            t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": args.d * n_e2e * world / (ms_e2e / 1e3), "unit": "elements/s",
+               "h2d_bytes_per_step": 4 * args.d, "d2h_bytes_per_step": 8 * args.d, "steps": n_e2e}
+        ctx.check(what="bench e2e")
+
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    # ---- variants: per-lambda and FP64 arithmetic / FP64 storage throughput, error at 2^20
+    variants = None
+    if not args.no_variants and rank == 0:
+        variants = {}
+        reps = 20
+        for lam in LAMBDAS:
+            for prec in ("fp32comp", "fp64"):
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(reps):
+                    ws.prox(w, lam, prec, ctx=ctx, out=out, n_clusters=nc)
+                b.record(stream)
+                torch.cuda.synchronize()
+                variants[f"f32_{prec}_lam{lam:g}"] = {"elements_per_s": args.d * reps / (a.elapsed_time(b) / 1e3),
+                                                      "clusters": int(nc.item())}
+        w64 = w.double()
+        out64 = torch.empty_like(w64)
+        for lam in LAMBDAS:
+            ws.prox(w64, lam, "fp64", ctx=ctx, out=out64, n_clusters=nc)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                ws.prox(w64, lam, "fp64", ctx=ctx, out=out64, n_clusters=nc)
+            b.record(stream)
+            torch.cuda.synchronize()
+            variants[f"f64_fp64_lam{lam:g}"] = {"elements_per_s": args.d * reps / (a.elapsed_time(b) / 1e3)}
+        del w64, out64
+        ctx.check(what="bench variants")
+        # error against the oracle on a 2^20 prefix (full comparison; oracle on host)
+        import oracle
+
+        n = 1 << 20
+        ws_np = w_np[:n]
+        xs = torch.from_numpy(ws_np).to(dev)
+        errs = {}
+        for lam in LAMBDAS:
+            ref, ref_ids, _ = oracle.prox(ws_np, lam)
+            scale = float(np.abs(ws_np).max()) + lam
+            for prec in ("fp32comp", "fp64"):
+                o, i, _ = ws.prox(xs, lam, prec, ctx=ctx)
+                err = float(np.abs(o.cpu().numpy().astype(np.float64) - ref).max()) / scale
+                same = bool(np.array_equal(i.cpu().numpy(), ref_ids))
+                errs[f"{prec}_lam{lam:g}"] = {"max_err_rel_to_max_w_plus_lambda": err, "partition_equal": same}
+        variants["error_vs_oracle_2^20"] = errs
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        import oracle
+
+        oracle.build()
+        n = 1 << 22
+        rate, dt = oracle_rate(w_np[:n], 6)
+        cpu = {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {n} elements of the workload vector, 6 calls cycling lambda ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 values / i128 fixed-point sums", "data": "synthetic",
+            "config": config_dict(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks, "kernels": shares, "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

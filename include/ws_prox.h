@@ -137,6 +137,20 @@ void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max);
  * Test hook for bit-exact sort parity. */
 ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, void* stream);
 
+/* Per-kernel timing for benchmarks.  ws_debug_profile(ctx, 1) starts
+ * recording a CUDA event pair around every kernel the context launches (on
+ * the launching stream) and clears the totals; 0 stops recording.
+ * ws_debug_profile_read synchronises on the last recorded event and returns
+ * the summed duration and launch count of one kernel kind (0 <= kind <
+ * number of kinds; ws_debug_kernel_name(kind) names it and returns NULL past
+ * the last kind). */
+ws_status ws_debug_profile(ws_ctx* ctx, int enable);
+ws_status ws_debug_profile_read(ws_ctx* ctx, int kind, double* total_ms, int64_t* count);
+const char* ws_debug_kernel_name(int kind);
+
+/* Number of kernels this context has launched since it was created. */
+int64_t ws_debug_launch_count(ws_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

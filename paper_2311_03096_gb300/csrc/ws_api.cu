@@ -29,6 +29,9 @@ struct ws_ctx {
     int64_t small_max_override = -1;
     std::vector<PlanCacheEntry> cache;
     std::mutex mu;
+    WsProf prof;
+    double prof_ms[WSK_COUNT] = {};
+    long long prof_cnt[WSK_COUNT] = {};
 };
 
 struct ws_plan {
@@ -102,6 +105,7 @@ LargeWork<T> make_work(const ws_plan* p) {
     W.dir = p->dir;
     W.bsum = (T*)p->bsum;
     W.bcnt = p->bcnt;
+    W.prof = &p->ctx->prof;
     return W;
 }
 
@@ -248,7 +252,7 @@ ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, voi
                       int64_t* n_clusters, ws_prec prec, cudaStream_t st) {
     const int fp64 = prec == WS_PREC_FP64 ? 1 : 0;
     cudaError_t e = ws_launch_small<T>((const T*)values, p->d_offsets, p->d_small, p->n_small, lambdas, (T*)out, ids,
-                                       n_clusters, fp64, p->ctx->status, st);
+                                       n_clusters, fp64, p->ctx->status, st, &p->ctx->prof);
     if (e) return map_cuda(e);
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);
@@ -263,7 +267,7 @@ ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, voi
 template <typename T>
 ws_status run_backward(ws_plan* p, const void* g, const int32_t* ids, void* gin, cudaStream_t st) {
     cudaError_t e = ws_launch_small_backward<T>((const T*)g, ids, p->d_offsets, p->d_small, p->n_small, (T*)gin,
-                                                p->ctx->status, st);
+                                                p->ctx->status, st, &p->ctx->prof);
     if (e) return map_cuda(e);
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);
@@ -323,6 +327,11 @@ ws_status ws_ctx_create(ws_ctx** ctx, int device) {
 
 void ws_ctx_destroy(ws_ctx* ctx) {
     if (!ctx) return;
+    if (ctx->prof.ev) {
+        for (int i = 0; i < 2 * ctx->prof.cap; ++i) cudaEventDestroy(ctx->prof.ev[i]);
+        delete[] ctx->prof.ev;
+        delete[] ctx->prof.kind;
+    }
     for (auto& c : ctx->cache) ws_plan_destroy(c.plan);
     ctx->cache.clear();
     if (ctx->status) cudaFree(ctx->status);
@@ -381,7 +390,7 @@ ws_status ws_prox(ws_ctx* ctx, const void* w, int64_t d, double lambda, void* ou
     ws_plan* p = cached_plan(ctx, d, dtype, &st);
     if (!p) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    k_set_lambda<<<1, 1, 0, s>>>(p->d_lambda1, lambda);
+    WS_LAUNCH(&ctx->prof, WSK_MISC, s, (k_set_lambda<<<1, 1, 0, s>>>(p->d_lambda1, lambda)));
     if (cudaGetLastError() != cudaSuccess) return WS_ERR_CUDA;
     return ws_prox_batched(p, w, p->d_lambda1, out, cluster_ids, n_clusters, prec, stream);
 }
@@ -449,5 +458,50 @@ ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, voi
     }
     return map_cuda(e);
 }
+
+static const char* const kKernelNames[WSK_COUNT] = {"small", "hist", "hist_scan", "onesweep", "tile_hull",
+                                                     "tile_scan", "merge", "root", "table", "big_gaps", "lookup",
+                                                     "backward", "misc"};
+
+const char* ws_debug_kernel_name(int kind) {
+    return (kind >= 0 && kind < WSK_COUNT) ? kKernelNames[kind] : nullptr;
+}
+
+ws_status ws_debug_profile(ws_ctx* ctx, int enable) {
+    if (!ctx) return WS_ERR_INVALID;
+    WsProf& P = ctx->prof;
+    if (enable && !P.ev) {
+        P.cap = 1 << 14;
+        P.ev = new (std::nothrow) cudaEvent_t[2 * P.cap];
+        P.kind = new (std::nothrow) int[P.cap];
+        if (!P.ev || !P.kind) return WS_ERR_NOMEM;
+        for (int i = 0; i < 2 * P.cap; ++i)
+            if (cudaEventCreate(&P.ev[i]) != cudaSuccess) return WS_ERR_CUDA;
+    }
+    P.enabled = enable != 0;
+    P.n = 0;
+    for (int k = 0; k < WSK_COUNT; ++k) { ctx->prof_ms[k] = 0.0; ctx->prof_cnt[k] = 0; }
+    return WS_OK;
+}
+
+ws_status ws_debug_profile_read(ws_ctx* ctx, int kind, double* total_ms, int64_t* count) {
+    if (!ctx || kind < 0 || kind >= WSK_COUNT) return WS_ERR_INVALID;
+    WsProf& P = ctx->prof;
+    if (P.n > 0) {   // fold the recorded event pairs into the per-kind totals
+        if (cudaEventSynchronize(P.ev[2 * P.n - 1]) != cudaSuccess) return WS_ERR_CUDA;
+        for (int i = 0; i < P.n; ++i) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]) != cudaSuccess) return WS_ERR_CUDA;
+            ctx->prof_ms[P.kind[i]] += ms;
+            ctx->prof_cnt[P.kind[i]] += 1;
+        }
+        P.n = 0;
+    }
+    if (total_ms) *total_ms = ctx->prof_ms[kind];
+    if (count) *count = ctx->prof_cnt[kind];
+    return WS_OK;
+}
+
+int64_t ws_debug_launch_count(ws_ctx* ctx) { return ctx ? (int64_t)ctx->prof.launches : 0; }
 
 }  // extern "C"

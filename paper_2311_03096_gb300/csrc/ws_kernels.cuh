@@ -7,6 +7,33 @@ template <typename T> struct SmallCfg;
 template <> struct SmallCfg<float> { static constexpr int M = 16; static constexpr int CAP = 256 * 16; };
 template <> struct SmallCfg<double> { static constexpr int M = 8; static constexpr int CAP = 256 * 8; };
 
+// Opt-in per-launch timing (CUDA events recorded on the launching stream
+// around every kernel) and a launch counter.  Host-side only.
+enum WsKernelKind {
+    WSK_SMALL = 0, WSK_HIST, WSK_HIST_SCAN, WSK_ONESWEEP, WSK_TILE_HULL, WSK_TILE_SCAN, WSK_MERGE, WSK_ROOT,
+    WSK_TABLE, WSK_BIG_GAPS, WSK_LOOKUP, WSK_BWD, WSK_MISC, WSK_COUNT
+};
+struct WsProf {
+    bool enabled = false;
+    int cap = 0, n = 0;
+    cudaEvent_t* ev = nullptr;   // 2 * cap events
+    int* kind = nullptr;         // cap
+    long long launches = 0;
+    void begin(cudaStream_t st, int k) {
+        ++launches;
+        if (!enabled || n >= cap) return;
+        cudaEventRecord(ev[2 * n], st);
+        kind[n] = k;
+    }
+    void end(cudaStream_t st) {
+        if (!enabled || n >= cap) return;
+        cudaEventRecord(ev[2 * n + 1], st);
+        ++n;
+    }
+};
+#define WS_LAUNCH(PROF, KIND, ST, ...) \
+    do { (PROF)->begin((ST), (KIND)); __VA_ARGS__; (PROF)->end((ST)); } while (0)
+
 // Large-path tile geometry.
 constexpr int WS_SORT_NT = 512;              // threads per onesweep CTA
 constexpr int WS_SORT_ITEMS = 16;            // keys per thread
@@ -72,10 +99,10 @@ struct SegRuntime {
 template <typename T>
 cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
                             const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
-                            uint32_t* status, cudaStream_t st);
+                            uint32_t* status, cudaStream_t st, WsProf* prof);
 template <typename T>
 cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64_t* offsets, const int32_t* seg_list,
-                                     int n_list, T* gin, uint32_t* status, cudaStream_t st);
+                                     int n_list, T* gin, uint32_t* status, cudaStream_t st, WsProf* prof);
 
 // Large path workspace pointers (all device).
 template <typename T>
@@ -106,6 +133,7 @@ struct LargeWork {
     // backward
     T* bsum;                 // [n_keys + n_lseg]
     int32_t* bcnt;           // [n_keys + n_lseg]
+    WsProf* prof;            // host-side launch accounting
 };
 
 template <typename T>

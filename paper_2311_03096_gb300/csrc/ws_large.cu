@@ -446,28 +446,35 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
     size_t smem = sizeof(TileHullSmem);
     e = cudaFuncSetAttribute(k_tile_hull<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
-    k_tile_hull<T><<<W.n_hull_tiles, HNT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp, W.vx,
-                                                     W.nvert, W.tile_total, W.pieces, W.npieces, status);
-    k_tile_scan<<<W.n_lseg, 256, 0, st>>>(W.lsegs, W.tile_total, W.tile_offset);
+    WS_LAUNCH(W.prof, WSK_TILE_HULL, st,
+              (k_tile_hull<T><<<W.n_hull_tiles, HNT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp,
+                                                                W.vx, W.nvert, W.tile_total, W.pieces, W.npieces,
+                                                                status)));
+    WS_LAUNCH(W.prof, WSK_TILE_SCAN, st, (k_tile_scan<<<W.n_lseg, 256, 0, st>>>(W.lsegs, W.tile_total, W.tile_offset)));
     for (int l = 0; l < n_levels; ++l)
         if (level_counts[l] > 0)
-            k_merge<T><<<level_counts[l], 256, 0, st>>>(level_nodes[l], W.lsegs, lambdas, W.rt, W.vp, W.vx,
-                                                       W.tile_offset, W.pieces, W.npieces, status);
+            WS_LAUNCH(W.prof, WSK_MERGE, st,
+                      (k_merge<T><<<level_counts[l], 256, 0, st>>>(level_nodes[l], W.lsegs, lambdas, W.rt, W.vp, W.vx,
+                                                                  W.tile_offset, W.pieces, W.npieces, status)));
     e = cudaMemsetAsync(W.tile_piece, 0xff, sizeof(int32_t) * (size_t)W.n_hull_tiles, st);
     if (e) return e;
-    k_root<T><<<W.n_lseg, 256, 0, st>>>(W.lsegs, sorted, W.pieces, W.npieces, W.tile_piece, W.rt, n_clusters);
+    WS_LAUNCH(W.prof, WSK_ROOT, st,
+              (k_root<T><<<W.n_lseg, 256, 0, st>>>(W.lsegs, sorted, W.pieces, W.npieces, W.tile_piece, W.rt,
+                                                  n_clusters)));
     // big-gap list lives at the tail of the backward sum buffer (unused in the forward)
     uint32_t* ngaps = reinterpret_cast<uint32_t*>(W.bcnt);
     BigGap* gaps = reinterpret_cast<BigGap*>(W.bsum);
     int64_t gap_cap = (int64_t)((W.n_keys + W.n_lseg) * sizeof(T) / sizeof(BigGap));
     e = cudaMemsetAsync(ngaps, 0, sizeof(uint32_t), st);
     if (e) return e;
-    k_table<T><<<W.n_hull_tiles, 256, 0, st>>>(W.hull_tiles, W.lsegs, lambdas, W.rt, sorted, W.vp, W.vx,
-                                              W.tile_offset, W.pieces, W.npieces, W.tile_piece, W.table, W.dir,
-                                              gaps, ngaps, gap_cap, fp64, status);
-    k_big_gaps<<<1024, 256, 0, st>>>(gaps, ngaps, W.dir, gap_cap);
-    k_lookup<T><<<W.n_sort_tiles, 256, 0, st>>>(values, W.sort_tiles, W.lsegs, W.rt, W.table, W.dir, out, ids,
-                                               status);
+    WS_LAUNCH(W.prof, WSK_TABLE, st,
+              (k_table<T><<<W.n_hull_tiles, 256, 0, st>>>(W.hull_tiles, W.lsegs, lambdas, W.rt, sorted, W.vp, W.vx,
+                                                         W.tile_offset, W.pieces, W.npieces, W.tile_piece, W.table,
+                                                         W.dir, gaps, ngaps, gap_cap, fp64, status)));
+    WS_LAUNCH(W.prof, WSK_BIG_GAPS, st, (k_big_gaps<<<1024, 256, 0, st>>>(gaps, ngaps, W.dir, gap_cap)));
+    WS_LAUNCH(W.prof, WSK_LOOKUP, st,
+              (k_lookup<T><<<W.n_sort_tiles, 256, 0, st>>>(values, W.sort_tiles, W.lsegs, W.rt, W.table, W.dir, out,
+                                                          ids, status)));
     return cudaGetLastError();
 }
 
@@ -480,8 +487,10 @@ cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* 
     if (e) return e;
     e = cudaMemsetAsync(W.bcnt, 0, sizeof(int32_t) * slots, st);
     if (e) return e;
-    k_bwd_accum<T><<<W.n_sort_tiles, 256, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, W.bsum, W.bcnt, status);
-    k_bwd_apply<T><<<W.n_sort_tiles, 256, 0, st>>>(ids, W.sort_tiles, W.lsegs, W.bsum, W.bcnt, gin);
+    WS_LAUNCH(W.prof, WSK_BWD, st,
+              (k_bwd_accum<T><<<W.n_sort_tiles, 256, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, W.bsum, W.bcnt, status)));
+    WS_LAUNCH(W.prof, WSK_BWD, st,
+              (k_bwd_apply<T><<<W.n_sort_tiles, 256, 0, st>>>(ids, W.sort_tiles, W.lsegs, W.bsum, W.bcnt, gin)));
     return cudaGetLastError();
 }
 
@@ -489,7 +498,7 @@ template <typename T>
 cudaError_t ws_large_copy_sorted(const LargeWork<T>& W, const typename KeyOf<T>::K* sorted, T* dst,
                                  cudaStream_t st) {
     if (W.n_sort_tiles == 0) return cudaSuccess;
-    k_copy_sorted<T><<<W.n_sort_tiles, 256, 0, st>>>(sorted, W.sort_tiles, dst);
+    WS_LAUNCH(W.prof, WSK_MISC, st, (k_copy_sorted<T><<<W.n_sort_tiles, 256, 0, st>>>(sorted, W.sort_tiles, dst)));
     return cudaGetLastError();
 }
 

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, 
 template <typename T>
 cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
                             const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
-                            uint32_t* status, cudaStream_t st) {
+                            uint32_t* status, cudaStream_t st, WsProf* prof) {
     constexpr int NT = 256;
     constexpr int M = SmallCfg<T>::M;
     if (n_list <= 0) return cudaSuccess;
@@ -217,24 +217,26 @@ cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32
     auto kern = k_small<T, NT, M>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<n_list, NT, smem, st>>>(values, offsets, seg_list, lambdas, out, ids, n_clusters, fp64, status);
+    WS_LAUNCH(prof, WSK_SMALL, st,
+              (kern<<<n_list, NT, smem, st>>>(values, offsets, seg_list, lambdas, out, ids, n_clusters, fp64, status)));
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64_t* offsets, const int32_t* seg_list,
-                                     int n_list, T* gin, uint32_t* status, cudaStream_t st) {
+                                     int n_list, T* gin, uint32_t* status, cudaStream_t st, WsProf* prof) {
     constexpr int NT = 256;
     if (n_list <= 0) return cudaSuccess;
-    k_small_backward<T, NT, SmallCfg<T>::CAP><<<n_list, NT, 0, st>>>(g, ids, offsets, seg_list, gin, status);
+    WS_LAUNCH(prof, WSK_BWD, st,
+              (k_small_backward<T, NT, SmallCfg<T>::CAP><<<n_list, NT, 0, st>>>(g, ids, offsets, seg_list, gin, status)));
     return cudaGetLastError();
 }
 
 template cudaError_t ws_launch_small<float>(const float*, const int64_t*, const int32_t*, int, const double*, float*,
-                                            int32_t*, int64_t*, int, uint32_t*, cudaStream_t);
+                                            int32_t*, int64_t*, int, uint32_t*, cudaStream_t, WsProf*);
 template cudaError_t ws_launch_small<double>(const double*, const int64_t*, const int32_t*, int, const double*,
-                                             double*, int32_t*, int64_t*, int, uint32_t*, cudaStream_t);
+                                             double*, int32_t*, int64_t*, int, uint32_t*, cudaStream_t, WsProf*);
 template cudaError_t ws_launch_small_backward<float>(const float*, const int32_t*, const int64_t*, const int32_t*,
-                                                     int, float*, uint32_t*, cudaStream_t);
+                                                     int, float*, uint32_t*, cudaStream_t, WsProf*);
 template cudaError_t ws_launch_small_backward<double>(const double*, const int32_t*, const int64_t*,
-                                                      const int32_t*, int, double*, uint32_t*, cudaStream_t);
+                                                      const int32_t*, int, double*, uint32_t*, cudaStream_t, WsProf*);

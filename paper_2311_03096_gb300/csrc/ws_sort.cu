@@ -169,8 +169,8 @@ cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* stat
     if (e) return e;
     e = cudaMemsetAsync(W.tile_counter, 0, sizeof(uint32_t) * P, st);
     if (e) return e;
-    k_hist<T><<<W.n_sort_tiles, WS_SORT_NT, 0, st>>>(values, W.sort_tiles, W.hist, status);
-    k_hist_scan<<<W.n_lseg * P, 256, 0, st>>>(W.hist);
+    WS_LAUNCH(W.prof, WSK_HIST, st, (k_hist<T><<<W.n_sort_tiles, WS_SORT_NT, 0, st>>>(values, W.sort_tiles, W.hist, status)));
+    WS_LAUNCH(W.prof, WSK_HIST_SCAN, st, (k_hist_scan<<<W.n_lseg * P, 256, 0, st>>>(W.hist)));
     size_t smem = ws_onesweep_smem<T>();
     e = cudaFuncSetAttribute(k_onesweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
@@ -181,11 +181,11 @@ cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* stat
     for (int p = 0; p < P; ++p) {
         uint64_t* lb = W.lookback + (size_t)p * W.n_sort_tiles * 256;
         if (p == 0)
-            k_onesweep<T, true><<<W.n_sort_tiles, WS_SORT_NT, smem, st>>>(
-                values, nullptr, dst, W.sort_tiles, W.lsegs, W.hist, lb, W.tile_counter + p, p, status, spin_limit);
+            WS_LAUNCH(W.prof, WSK_ONESWEEP, st, (k_onesweep<T, true><<<W.n_sort_tiles, WS_SORT_NT, smem, st>>>(
+                values, nullptr, dst, W.sort_tiles, W.lsegs, W.hist, lb, W.tile_counter + p, p, status, spin_limit)));
         else
-            k_onesweep<T, false><<<W.n_sort_tiles, WS_SORT_NT, smem, st>>>(
-                values, src, dst, W.sort_tiles, W.lsegs, W.hist, lb, W.tile_counter + p, p, status, spin_limit);
+            WS_LAUNCH(W.prof, WSK_ONESWEEP, st, (k_onesweep<T, false><<<W.n_sort_tiles, WS_SORT_NT, smem, st>>>(
+                values, src, dst, W.sort_tiles, W.lsegs, W.hist, lb, W.tile_counter + p, p, status, spin_limit)));
         K* tmp = src; src = dst; dst = tmp;
     }
     *sorted = src;   // the buffer written last

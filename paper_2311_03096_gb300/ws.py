@@ -63,8 +63,16 @@ def _load():
             lib.ws_debug_set_small_max.argtypes = [_vp, _i64]
             lib.ws_debug_set_small_max.restype = None
             lib.ws_debug_sort.argtypes = [_vp, _vp, _vp, _vp]
+            lib.ws_debug_profile.argtypes = [_vp, ctypes.c_int]
+            lib.ws_debug_profile_read.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                                  ctypes.POINTER(_i64)]
+            lib.ws_debug_kernel_name.argtypes = [ctypes.c_int]
+            lib.ws_debug_kernel_name.restype = ctypes.c_char_p
+            lib.ws_debug_launch_count.argtypes = [_vp]
+            lib.ws_debug_launch_count.restype = _i64
             for f in ("ws_ctx_create", "ws_plan_create", "ws_prox_batched", "ws_prox", "ws_prox_backward_batched",
-                      "ws_prox_backward", "ws_get_status", "ws_debug_sort"):
+                      "ws_prox_backward", "ws_get_status", "ws_debug_sort", "ws_debug_profile",
+                      "ws_debug_profile_read"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -128,6 +136,28 @@ class Context:
 
     def set_small_max(self, n: int):
         _load().ws_debug_set_small_max(self.handle, int(n))
+
+    def profile(self, enable: bool):
+        """Start (and clear) or stop per-kernel event timing."""
+        _check(_load().ws_debug_profile(self.handle, 1 if enable else 0), "ws_debug_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (total_ms, launches)} recorded since profile(True)."""
+        res = {}
+        k = 0
+        while True:
+            name = _load().ws_debug_kernel_name(k)
+            if name is None:
+                break
+            ms, cnt = ctypes.c_double(0), _i64(0)
+            _check(_load().ws_debug_profile_read(self.handle, k, ctypes.byref(ms), ctypes.byref(cnt)), "profile_read")
+            if cnt.value:
+                res[name.decode()] = (ms.value, cnt.value)
+            k += 1
+        return res
+
+    def launch_count(self) -> int:
+        return int(_load().ws_debug_launch_count(self.handle))
 
     def __del__(self):
         try:
