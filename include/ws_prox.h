@@ -137,6 +137,37 @@ void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max);
  * Test hook for bit-exact sort parity. */
 ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, void* stream);
 
+/* Largest d accepted by ws_prox_backward_noalloc (2^20 elements). */
+#define WS_NOALLOC_MAX_ELEMS (1 << 20)
+
+/* Backward that allocates no device memory (the paper has no counterpart;
+ * this is a library convenience).  Same result as ws_prox_backward for one
+ * vector of d <= WS_NOALLOC_MAX_ELEMS elements: grad_in[i] = mean of
+ * grad_out over the cluster of i, clusters given by cluster_ids (0-based,
+ * < d) as written by the forward.  It exists for callers that must not call
+ * cudaMalloc/cudaFree where they run the backward: a framework that has
+ * already reserved the device memory for its own pool, a loop that cannot
+ * take the implicit device synchronisation of an allocation, or code running
+ * while a stream is captured.  Its per-cluster sums and counts live in one
+ * fixed array of device memory (12 MiB) that the library holds on every GPU
+ * that loads it until the process exits.
+ *   - grad_out, cluster_ids, grad_in: DEVICE pointers owned by the caller
+ *     (d elements of dtype, d int32, d elements of dtype); grad_in may alias
+ *     grad_out.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before capturing any stream on that device.  No call allocates.
+ *   - d > WS_NOALLOC_MAX_ELEMS or d < 0 returns WS_ERR_INVALID and enqueues
+ *     nothing; d == 0 is a no-op.  Ids outside [0, d) are skipped and leave
+ *     their grad_in entry unchanged.
+ *   - All calls share the one array: calls whose kernels may overlap on the
+ *     GPU (different streams without ordering, several host threads) race
+ *     and give wrong results; order them on one stream.  Each call clears the
+ *     part of the array it uses before accumulating.
+ *   - Stream-ordered on `stream`; the host is not synchronised. */
+ws_status ws_prox_backward_noalloc(const void* grad_out, const int32_t* cluster_ids, int64_t d,
+                                   void* grad_in, ws_dtype dtype, void* stream);
+
 /* Per-kernel timing for benchmarks.  ws_debug_profile(ctx, 1) starts
  * recording a CUDA event pair around every kernel the context launches (on
  * the launching stream) and clears the totals; 0 stops recording.

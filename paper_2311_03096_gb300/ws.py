@@ -189,6 +189,22 @@ def prox_backward(grad_out: torch.Tensor, ids: torch.Tensor, ctx: Context | None
     return gin
 
 
+NOALLOC_MAX_ELEMS = 1 << 20
+
+
+def prox_backward_noalloc(grad_out: torch.Tensor, ids: torch.Tensor, grad_in: torch.Tensor, stream=None):
+    """Backward for one vector (d <= 2^20) through ws_prox_backward_noalloc: no
+    device allocation inside the call; scratch is the library's fixed device
+    array.  For callers that must not allocate where the backward runs."""
+    lib_ = _load()
+    fn = lib_.ws_prox_backward_noalloc
+    fn.argtypes = [_vp, _vp, _i64, _vp, ctypes.c_int, _vp]
+    fn.restype = ctypes.c_int
+    _check(fn(_ptr(grad_out), _ptr(ids), grad_out.shape[0], _ptr(grad_in), _dtype_code(grad_out.dtype),
+              _stream(stream)), "ws_prox_backward_noalloc")
+    return grad_in
+
+
 class Plan:
     """A ws_plan for a fixed batch layout (host offsets, int64, n_seg + 1 entries)."""
 
