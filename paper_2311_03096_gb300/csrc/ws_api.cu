@@ -59,6 +59,7 @@ struct ws_plan {
     uint32_t* hist = nullptr;
     uint64_t* lookback = nullptr;
     uint32_t* tile_counter = nullptr;
+    uint32_t* epoch = nullptr;
     uint16_t* vp = nullptr;
     i128* vx = nullptr;
     int32_t* nvert = nullptr;
@@ -92,6 +93,7 @@ LargeWork<T> make_work(const ws_plan* p) {
     W.hist = p->hist;
     W.lookback = p->lookback;
     W.tile_counter = p->tile_counter;
+    W.epoch = p->epoch;
     W.vp = p->vp;
     W.vx = p->vx;
     W.nvert = p->nvert;
@@ -172,7 +174,7 @@ ws_status build_plan(ws_plan* p) {
         ls.dir_cap_log2 = ceil_log2(len);
         ls.dir_pos = dir_pos;
         dir_pos += ((int64_t)1 << ls.dir_cap_log2) + 1;
-        kpos += len;
+        kpos += (len + 3) & ~(int64_t)3;   // keep every segment's keys 16-byte aligned
         lsegs.push_back(ls);
     }
     p->n_small = (int)small.size();
@@ -222,6 +224,10 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->hist, sizeof(uint32_t) * p->n_lseg * P * 256))) return st;
     if ((st = plan_alloc(p, (void**)&p->lookback, sizeof(uint64_t) * (size_t)P * p->n_sort_tiles * 256))) return st;
     if ((st = plan_alloc(p, (void**)&p->tile_counter, sizeof(uint32_t) * P))) return st;
+    if ((st = plan_alloc(p, (void**)&p->epoch, sizeof(uint32_t)))) return st;
+    if (cudaMemset(p->epoch, 0, sizeof(uint32_t)) != cudaSuccess) return WS_ERR_CUDA;
+    if (cudaMemset(p->lookback, 0, sizeof(uint64_t) * (size_t)P * p->n_sort_tiles * 256) != cudaSuccess)
+        return WS_ERR_CUDA;
     if ((st = plan_alloc(p, (void**)&p->vp, sizeof(uint16_t) * nh * (WS_HULL_TILE + 1)))) return st;
     if ((st = plan_alloc(p, (void**)&p->vx, sizeof(i128) * nh * (WS_HULL_TILE + 1)))) return st;
     if ((st = plan_alloc(p, (void**)&p->nvert, sizeof(int32_t) * nh))) return st;

@@ -55,47 +55,185 @@ __device__ __forceinline__ V ws_block_excl_scan(V v, V* wsum, V* total) {
 }
 
 // ---------------------------------------------------------------------------
+// Fixed-point prefix sums of a sorted tile (points 0..n).
+// Per-point arrays are stored at padded index p + p/M so that the threads of
+// a warp, which own consecutive chunks of M points, hit distinct banks.
+// Narrow tiles (n * (q_{n-1} - q_0) <= 2^62) store D_p = sum_{j<p} (q_j - q_0)
+// in s64; wide tiles store the chunk-relative prefix in s64 and the chunk
+// starts in base (128-bit).  Returns true for a narrow tile.  Contains
+// __syncthreads; ends synchronised.
+// ---------------------------------------------------------------------------
+template <int M> __device__ __forceinline__ int ws_sidx(int p) { return p + p / M; }
+
+template <int NT, int M>
+struct TilePrefix {
+    int64_t s64[NT * M + 1 + NT + 1];
+    i128 base[NT + 1];
+    i128 wsum128[NT / 32];
+    long long wsum64[NT / 32];
+};
+
+// Representation of a tile's prefix sums.
+enum { WS_TILE_WIDE = 0, WS_TILE_NARROW = 1, WS_TILE_BINADE = 2 };
+
+// kr[i] = key of sorted element first + i (first = threadIdx.x * M); k0, kn =
+// keys of elements 0 and n - 1.  Modes:
+//   BINADE: all keys share sign and exponent, so key - k0 is the value
+//           difference in ulps of that binade, exactly; s64 holds prefix sums
+//           of (key - k0) in ulp units; one ulp = 2^sh global fixed-point units
+//           (sh >= 0 is required: otherwise the global image truncates).
+//   NARROW: s64 holds D_p = sum (q_j - q_0) in global units.
+//   WIDE:   s64 holds chunk-relative prefixes, base[] the chunk starts (128-bit).
+// q0_out = global fixed-point image of element 0; total_out = X_n (global).
+template <typename T, int NT, int M>
+__device__ int ws_tile_prefix(TilePrefix<NT, M>& tp, const typename KeyOf<T>::K (&kr)[M], typename KeyOf<T>::K k0,
+                              typename KeyOf<T>::K kn, int n, int emax, int64_t& q0_out, i128& total_out,
+                              int& binade_sh) {
+    typedef KeyOf<T> KO;
+    typedef typename KO::K K;
+    constexpr int CAP = NT * M;
+    const int t = threadIdx.x;
+    const int first = t * M;
+    const T x0 = KO::from_key(k0);
+    const int64_t q0 = ws_fixed<T>(x0, emax);
+    q0_out = q0;
+    const int sh = ws_eff_exp(x0) - emax + KO::FIX_OFS;
+    const bool same_binade = ((k0 ^ kn) >> KO::MANT) == 0 && sh >= 0;
+    const uint64_t krange = (uint64_t)(kn - k0);
+    int mode;
+    if (same_binade && krange <= ((uint64_t)1 << 62) / (uint64_t)n) {
+        mode = WS_TILE_BINADE;
+    } else {
+        const int64_t qn = ws_fixed<T>(KO::from_key(kn), emax);
+        mode = ((uint64_t)(qn - q0) <= ((uint64_t)1 << 62) / (uint64_t)n) ? WS_TILE_NARROW : WS_TILE_WIDE;
+    }
+    binade_sh = sh;
+    long long run = 0;
+    if (mode == WS_TILE_BINADE) {
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (first + i < n) run += (long long)(kr[i] - k0);
+    } else {
+        const int64_t sub = mode == WS_TILE_NARROW ? q0 : 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (first + i < n) run += ws_fixed<T>(KO::from_key(kr[i]), emax) - sub;
+    }
+    if (mode != WS_TILE_WIDE) {
+        long long tot;
+        long long acc = ws_block_excl_scan<NT, long long>(run, tp.wsum64, &tot);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int p = first + i;
+            if (p <= n) tp.s64[ws_sidx<M>(p)] = acc;
+            if (p < n)
+                acc += (mode == WS_TILE_BINADE) ? (long long)(kr[i] - k0)
+                                                : ws_fixed<T>(KO::from_key(kr[i]), emax) - q0;
+        }
+        if (t == 0 && n == CAP) tp.s64[ws_sidx<M>(CAP)] = tot;
+        total_out = (mode == WS_TILE_BINADE) ? (i128)n * (i128)q0 + ((i128)tot << sh)
+                                             : (i128)tot + (i128)n * (i128)q0;
+    } else {
+        i128 tot;
+        const i128 ex = ws_block_excl_scan<NT, i128>((i128)run, tp.wsum128, &tot);
+        long long acc = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int p = first + i;
+            if (p <= n) tp.s64[ws_sidx<M>(p)] = acc;
+            if (p < n) acc += ws_fixed<T>(KO::from_key(kr[i]), emax);
+        }
+        tp.base[t] = ex;
+        if (t == 0) { tp.base[NT] = tot; if (n == CAP) tp.s64[ws_sidx<M>(CAP)] = 0; }
+        total_out = tot;
+    }
+    __syncthreads();
+    return mode;
+}
+
+// Global fixed-point prefix X_p for any tile mode.
+template <int M>
+__device__ __forceinline__ i128 ws_tile_X(const int64_t* s64, const i128* base, int mode, int64_t q0, int sh, int p) {
+    const int64_t v = s64[ws_sidx<M>(p)];
+    if (mode == WS_TILE_BINADE) return (i128)p * (i128)q0 + ((i128)v << sh);
+    if (mode == WS_TILE_NARROW) return (i128)p * (i128)q0 + (i128)v;
+    return base[p / M] + (i128)v;
+}
+
+// lambda * 2^L / (d - 1) as float for the FP32 filter; usable if finite and
+// small enough that muq * (c - a) * n1 * n2 stays far from overflow.
+__device__ __forceinline__ float ws_muq(double lam, const SegConst& sc, bool& usable) {
+    double m = (sc.d > 1) ? ldexp(lam, sc.L) / (double)(sc.d - 1) : 0.0;
+    usable = (m == m) && m < 1.0e26;
+    return usable ? (float)m : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
 // Stable ranking of a CTA's keys by one 8-bit digit.
 // Arrangement: warp w owns positions [w*32*ITEMS, (w+1)*32*ITEMS); item k of
-// lane l is position w*32*ITEMS + k*32 + l, so processing k in order and lanes
-// in order visits positions in order (stability).  Returns, per item, the
-// position of the key in the digit-sorted tile; digit_count/digit_start
-// (shared, 256 entries) receive the tile histogram and its exclusive scan.
-// whist: shared [NW][256] uint32.
+// lane l is position w*32*ITEMS + k*32 + l.  The warp's items are split into
+// NC contiguous runs ("chains") of ITEMS/NC items; each chain keeps its own
+// digit counters, so the NC read-modify-write chains through shared memory
+// are independent and overlap.  Within a chain, processing items in order
+// and lanes in order (match_any + popc) visits positions in order; chains
+// and warps are combined in position order, so the ranking is stable.
+// Returns, per item, the position of the key in the digit-sorted tile;
+// digit_count/digit_start (shared, 256 entries) receive the tile histogram
+// and its exclusive scan.  whist: shared [NT/32][NC][256] uint32.
 // ---------------------------------------------------------------------------
-template <int NT, int ITEMS>
+// Lanes of the warp holding the same 8-bit digit (valid lanes only), built
+// from eight ballots; measured faster than __match_any_sync on sm_103a.
+__device__ __forceinline__ unsigned ws_peers8(uint32_t dg, bool valid) {
+    unsigned m = __ballot_sync(WS_FULL_MASK, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const unsigned bal = __ballot_sync(WS_FULL_MASK, (dg >> b) & 1u);
+        m &= ((dg >> b) & 1u) ? bal : ~bal;
+    }
+    return m;
+}
+
+template <int NT, int ITEMS, int NC>
 __device__ __forceinline__ void ws_rank_digits(const uint32_t (&dig)[ITEMS], const bool (&valid)[ITEMS],
                                                int (&pos)[ITEMS], uint32_t* whist, uint32_t* digit_count,
-                                               uint32_t* digit_start, uint32_t* scratch32) {
-    constexpr int NW = NT / 32;
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t* my = whist + w * 256;
-    for (int i = lane; i < 256; i += 32) my[i] = 0;
+                                               uint32_t* digit_start) {
+    static_assert(ITEMS % NC == 0, "items must split evenly into chains");
+    constexpr int NW = NT / 32, IPC = ITEMS / NC;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t* my = whist + w * NC * 256;
+    for (int i = lane; i < NC * 256; i += 32) my[i] = 0;
     __syncwarp();
-    unsigned lt = (1u << lane) - 1u;
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-        unsigned act = __ballot_sync(WS_FULL_MASK, valid[k]);
-        uint32_t dg = valid[k] ? dig[k] : 256u + lane;   // invalid lanes get private digits
-        unsigned peers = __match_any_sync(WS_FULL_MASK, dg) & act;
-        int before = 0;
-        if (valid[k]) before = (int)my[dg];
+    for (int st = 0; st < IPC; ++st) {
+        unsigned peers[NC];
+        int before[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int k = c * IPC + st;
+            peers[c] = ws_peers8(dig[k], valid[k]);
+            before[c] = valid[k] ? (int)my[c * 256 + dig[k]] : 0;
+        }
         __syncwarp();
-        if (valid[k]) {
-            int r = __popc(peers & lt);
-            pos[k] = before + r;
-            if (r == 0) my[dg] = (uint32_t)(before + __popc(peers));
-        } else {
-            pos[k] = -1;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const int k = c * IPC + st;
+            if (valid[k]) {
+                const int r = __popc(peers[c] & lt);
+                pos[k] = before[c] + r;
+                if (r == 0) my[c * 256 + dig[k]] = (uint32_t)(before[c] + __popc(peers[c]));
+            } else {
+                pos[k] = -1;
+            }
         }
         __syncwarp();
     }
     __syncthreads();
-    // per digit: exclusive scan across warps, tile count
+    // per digit: exclusive scan across (warp, chain) in position order, tile count
     for (int dgt = threadIdx.x; dgt < 256; dgt += NT) {
         uint32_t run = 0;
-        for (int ww = 0; ww < NW; ++ww) {
-            uint32_t c = whist[ww * 256 + dgt];
+        for (int ww = 0; ww < NW * NC; ++ww) {
+            const uint32_t c = whist[ww * 256 + dgt];
             whist[ww * 256 + dgt] = run;
             run += c;
         }
@@ -104,24 +242,23 @@ __device__ __forceinline__ void ws_rank_digits(const uint32_t (&dig)[ITEMS], con
     __syncthreads();
     // exclusive scan over the 256 digits
     if (threadIdx.x < 32) {
-        uint32_t v[8], s = 0;
+        uint32_t v[8], sum = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) { v[i] = digit_count[lane * 8 + i]; s += v[i]; }
-        uint32_t inc = s;
+        for (int i = 0; i < 8; ++i) { v[i] = digit_count[lane * 8 + i]; sum += v[i]; }
+        uint32_t inc = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t t = __shfl_up_sync(WS_FULL_MASK, inc, o);
-            if (lane >= o) inc += t;
+            const uint32_t tt = __shfl_up_sync(WS_FULL_MASK, inc, o);
+            if (lane >= o) inc += tt;
         }
-        uint32_t run = inc - s;
+        uint32_t run = inc - sum;
 #pragma unroll
         for (int i = 0; i < 8; ++i) { digit_start[lane * 8 + i] = run; run += v[i]; }
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k)
-        if (valid[k]) pos[k] += (int)(digit_start[dig[k]] + whist[w * 256 + dig[k]]);
-    (void)scratch32;
+        if (valid[k]) pos[k] += (int)(digit_start[dig[k]] + whist[(w * NC + k / IPC) * 256 + dig[k]]);
 }
 
 // ---------------------------------------------------------------------------
@@ -140,23 +277,355 @@ __device__ __forceinline__ void ws_rank_digits(const uint32_t (&dig)[ITEMS], con
 // ---------------------------------------------------------------------------
 template <int NT, int M>
 struct HullSmem {
-    uint16_t H[NT * (M + 1)];   // chunk hull vertex lists (tile-local point indices)
+    uint16_t H[(M + 1) * NT];   // chunk hull lists, transposed: entry k of chunk c at k*NT + c
     uint16_t lo[NT], hi[NT];    // surviving range of each list
-    int cum[NT + 1];            // exclusive scan of surviving counts
-    int res_flag[NT], res_i[NT], res_j[NT];
+    int cum[NT + 1];            // exclusive scan of surviving counts (warp- or CTA-relative)
+    int wtot[NT / 32];          // per-warp totals during the warp levels
+    int res_i[NT], res_j[NT];
     int wsum_i[NT / 32];
 };
 
-// rank -> point within the children of a node (chunks [c0, c1), ranks relative to cum[c0])
+// ---------------------------------------------------------------------------
+// The hull test on tile-local points.
+//
+// Narrow tiles: A, B are sums of deviations (q - q_0); the test
+// (B n1 - A n2) > mu 2^L (c - a) n1 n2 (the q_0 terms cancel) is decided in
+// FP32 with a rigorous error bound (each operand carries <= 2^-24 relative
+// rounding; the bound allows ~16 of them); only near-ties fall through to
+// the exact integer test.  Wide tiles: exact test only.
+// ---------------------------------------------------------------------------
+static __device__ __noinline__ bool ws_convex_exact(i128 Xa, i128 Xb, i128 Xc, int a, int b, int c,
+                                                    const SegConst& sc) {
+    return ws_convex(Xa, Xb, Xc, a, b, c, sc);
+}
+
+template <int M, bool NARROW>
+struct TilePts {
+    const int64_t* s64;
+    const i128* base;
+    int64_t q0;
+    float muq;
+    bool fast;
+    __device__ __forceinline__ int64_t v(int p) const { return s64[ws_sidx<M>(p)]; }
+    __device__ __forceinline__ i128 Xv(int p, int64_t vp) const {
+        return NARROW ? (i128)vp + (i128)p * (i128)q0 : base[p / M] + (i128)vp;
+    }
+    __device__ __forceinline__ i128 X(int p) const { return Xv(p, v(p)); }
+    __device__ __forceinline__ bool convex_v(int a, int64_t va, int b, int64_t vb, int c, int64_t vc,
+                                             const SegConst& sc) const {
+        if (NARROW && fast) {
+            const float n1 = (float)(b - a), n2 = (float)(c - b);
+            const float fB = (float)(vc - vb) * n1;
+            const float fA = (float)(vb - va) * n2;
+            const float rhs = muq * (float)(c - a) * n1 * n2;
+            const float diff = (fB - fA) - rhs;
+            const float err = 1.0e-6f * (fabsf(fB) + fabsf(fA) + rhs);
+            if (diff > err) return true;
+            if (diff < -err) return false;
+        }
+        return ws_convex_exact(Xv(a, va), Xv(b, vb), Xv(c, vc), a, b, c, sc);
+    }
+    __device__ __forceinline__ bool convex(int a, int b, int c, const SegConst& sc) const {
+        return convex_v(a, v(a), b, v(b), c, v(c), sc);
+    }
+};
+
+// Exact test for tiles inside one binade.  s64 holds prefix sums of ulp
+// deviations, so A, B are 64-bit integers and Delta = B n1 - A n2 is exact in
+// 128 bits; Delta (d-1) is compared with mlam (c-a) n1 n2 2^s by bit length,
+// then by aligned 128-bit magnitudes -- no rounding anywhere.
+static __device__ __noinline__ bool ws_convex_binade_exact(int64_t A, int64_t B, int64_t n1, int64_t n2,
+                                                           int64_t cma, const SegConst& sc) {
+    const i128 D = (i128)B * (i128)n1 - (i128)A * (i128)n2;
+    if (D <= 0) return false;
+    if (sc.mlam == 0) return true;
+    const u128 Lv = (u128)D * (u128)sc.dm1;
+    const u128 Rv = (u128)sc.mlam * (u128)((uint64_t)cma * (uint64_t)(n1 * n2));
+    const int bl = ws_bitlen128(Lv), br = ws_bitlen128(Rv);
+    const int s = sc.s;
+    const int el = bl + (s < 0 ? -s : 0), er = br + (s > 0 ? s : 0);
+    if (el != er) return el > er;
+    return (Lv << (128 - bl)) > (Rv << (128 - br));
+}
+
+// Binade tiles: FP32 filter with a rigorous bound (as in TilePts), then the
+// exact integer test for near-ties.
+template <int M>
+struct TilePtsBinade {
+    const int64_t* s64;
+    float muq;   // lambda 2^L_tile / (d - 1)
+    bool fast;
+    __device__ __forceinline__ int64_t v(int p) const { return s64[ws_sidx<M>(p)]; }
+    __device__ __forceinline__ bool convex_v(int a, int64_t va, int b, int64_t vb, int c, int64_t vc,
+                                             const SegConst& sc) const {
+        const int64_t A = vb - va, B = vc - vb;
+        if (fast) {
+            const float n1 = (float)(b - a), n2 = (float)(c - b);
+            const float fB = (float)B * n1;
+            const float fA = (float)A * n2;
+            const float rhs = muq * (float)(c - a) * n1 * n2;
+            const float diff = (fB - fA) - rhs;
+            const float err = 4.0e-7f * (fabsf(fB) + fabsf(fA) + rhs);
+            if (diff > err) return true;
+            if (diff < -err) return false;
+        }
+        return ws_convex_binade_exact(A, B, b - a, c - b, c - a, sc);
+    }
+    __device__ __forceinline__ bool convex(int a, int b, int c, const SegConst& sc) const {
+        return convex_v(a, v(a), b, v(b), c, v(c), sc);
+    }
+};
+
+// Rank -> point in the hull of chunks [c0, c1) (ranks relative to cum[c0]).
 template <int NT, int M>
 __device__ __forceinline__ int ws_hull_point(const HullSmem<NT, M>& s, int c0, int c1, int r) {
-    int target = r + s.cum[c0];
+    const int target = r + s.cum[c0];
     int lo = c0, hi = c1 - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
+        const int mid = (lo + hi + 1) >> 1;
         if (s.cum[mid] <= target) lo = mid; else hi = mid - 1;
     }
-    return (int)s.H[lo * (M + 1) + s.lo[lo] + (target - s.cum[lo])];
+    return (int)s.H[(s.lo[lo] + (target - s.cum[lo])) * NT + lo];
+}
+
+// Bridge search between the hulls of chunks [cL0, cL1) (ranks 0..p) and
+// [cR0, cR1) (ranks 0..q) that share their junction point L_p = R_0.
+// On return: flag 0 = the junction stays a vertex (keep L, drop R_0, the
+// duplicate); flag 1 = the merged hull is L[0..istar] + R[jstar..q].
+// L_i survives iff it is strictly below the chord from L_{i-1} to its
+// tangent point on R; survivors form a prefix of L, so istar is found by a
+// gallop from the junction plus bisection, and each tangent the same way.
+template <int NT, int M, class Pts>
+struct TileBridge {
+    const HullSmem<NT, M>& s;
+    const Pts& P;
+    const SegConst& sc;
+    int cL0, cL1, cR0, cR1, q;
+    __device__ __forceinline__ int Lpt(int r) const { return ws_hull_point<NT, M>(s, cL0, cL1, r); }
+    __device__ __forceinline__ int Rpt(int r) const { return ws_hull_point<NT, M>(s, cR0, cR1, r); }
+    // R_{j+1} on or below the line (L_i, R_j): keep moving right
+    __device__ __forceinline__ bool right(int pi, int64_t vi, int j) const {
+        const int rj = Rpt(j), rk = Rpt(j + 1);
+        return !P.convex_v(pi, vi, rj, P.v(rj), rk, P.v(rk), sc);
+    }
+    __device__ __forceinline__ int tangent(int pi, int64_t vi) const {
+        if (!right(pi, vi, 0)) return 0;
+        int good = 0, step = 1, bad;
+        while (true) {
+            const int j = good + step;
+            if (j >= q) { bad = q; break; }
+            if (right(pi, vi, j)) { good = j; step <<= 1; } else { bad = j; break; }
+        }
+        while (bad - good > 1) {
+            const int mid = (good + bad) >> 1;
+            if (right(pi, vi, mid)) good = mid; else bad = mid;
+        }
+        return bad;
+    }
+    __device__ __forceinline__ bool survives(int i, int* jt) const {
+        const int pi = Lpt(i);
+        const int64_t vi = P.v(pi);
+        *jt = tangent(pi, vi);
+        if (i == 0) return true;
+        const int pm = Lpt(i - 1), pt = Rpt(*jt);
+        return P.convex_v(pm, P.v(pm), pi, vi, pt, P.v(pt), sc);
+    }
+    // galloping search (logarithmic on long bridges)
+    __device__ __noinline__ void search(int p, int& istar, int& jstar) const {
+        int jt;
+        if (survives(p - 1, &jt)) { istar = p - 1; jstar = jt; return; }
+        int bad = p - 1, good = 0, step = 1, jgood = 0;
+        while (true) {
+            const int i = p - 1 - step;
+            if (i <= 0) { good = 0; survives(0, &jgood); break; }
+            int jj;
+            if (survives(i, &jj)) { good = i; jgood = jj; break; }
+            bad = i; step <<= 1;
+        }
+        while (bad - good > 1) {
+            const int mid = (good + bad) >> 1;
+            int jj;
+            if (survives(mid, &jj)) { good = mid; jgood = jj; } else bad = mid;
+        }
+        istar = good; jstar = jgood;
+    }
+    // cursor over a chunk range: (chunk, entry); rank = cum[c] - cum[c0] + (k - lo[c]).
+    // Moving across chunk lists jumps over empty chunks with a binary search
+    // on the rank scan (cum), not a linear walk.
+    __device__ __forceinline__ void locate(int c0, int c1, int r, int& c, int& k) const {
+        const int target = r + s.cum[c0];
+        int lo = c0, hi = c1 - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s.cum[mid] <= target) lo = mid; else hi = mid - 1;
+        }
+        c = lo;
+        k = s.lo[lo] + (target - s.cum[lo]);
+    }
+    __device__ __forceinline__ bool prevL(int& c, int& k) const {
+        if (k > s.lo[c]) { --k; return true; }
+        const int r = s.cum[c] - s.cum[cL0] - 1;   // rank of the previous vertex of L
+        if (r < 0) return false;
+        locate(cL0, c, r, c, k);
+        return true;
+    }
+    __device__ __forceinline__ bool nextR(int& c, int& k) const {
+        if (k + 1 < s.hi[c]) { ++k; return true; }
+        const int r = s.cum[c] - s.cum[cR0] + (s.hi[c] - s.lo[c]);   // rank of the next vertex of R
+        if (r > q) return false;
+        locate(cR0, cR1, r, c, k);
+        return true;
+    }
+    __device__ __forceinline__ int at(int c, int k) const { return (int)s.H[k * NT + c]; }
+    // Bridge: start at the junction and walk outward (the linear merge of
+    // two convex chains); after a few steps fall back to the gallop.
+    __device__ void run(int p, int& flag, int& istar, int& jstar) const {
+        flag = 0; istar = p; jstar = 0;
+        if (p <= 0 || q <= 0) return;
+        // cursors on L_{p-1} and R_1 (the junction J = L_p = R_0 sits between them)
+        int lc, lk, rc, rk, jc, jk;
+        locate(cL0, cL1, p - 1, lc, lk);
+        locate(cR0, cR1, 0, jc, jk);
+        locate(cR0, cR1, 1, rc, rk);
+        int li = at(lc, lk), rj = at(rc, rk);
+        int64_t vli = P.v(li), vrj = P.v(rj);
+        {
+            const int pj = at(jc, jk);
+            if (P.convex_v(li, vli, pj, P.v(pj), rj, vrj, sc)) return;   // junction stays a vertex
+        }
+        flag = 1;
+        int steps = 0;
+        constexpr int WALK_MAX = 24;
+        while (true) {
+            bool moved = false;
+            while (true) {   // move left while L_{i-1} is on/below the line (L_i, R_j)
+                int c2 = lc, k2 = lk;
+                if (!prevL(c2, k2)) break;
+                const int lm = at(c2, k2);
+                const int64_t vlm = P.v(lm);
+                if (P.convex_v(lm, vlm, li, vli, rj, vrj, sc)) break;
+                lc = c2; lk = k2; li = lm; vli = vlm; moved = true;
+                if (++steps > WALK_MAX) { search(p, istar, jstar); return; }
+            }
+            while (true) {   // move right while R_{j+1} is on/below the line (L_i, R_j)
+                int c2 = rc, k2 = rk;
+                if (!nextR(c2, k2)) break;
+                const int rn = at(c2, k2);
+                const int64_t vrn = P.v(rn);
+                if (P.convex_v(li, vli, rj, vrj, rn, vrn, sc)) break;
+                rc = c2; rk = k2; rj = rn; vrj = vrn; moved = true;
+                if (++steps > WALK_MAX) { search(p, istar, jstar); return; }
+            }
+            if (!moved) break;
+        }
+        istar = s.cum[lc] - s.cum[cL0] + (lk - s.lo[lc]);
+        jstar = s.cum[rc] - s.cum[cR0] + (rk - s.lo[rc]);
+    }
+};
+
+// Narrow this chunk's surviving range after the merge of node `node`
+// (children [node, node+half) and [node+half, node+2half)).
+template <int NT, int M>
+__device__ __forceinline__ void ws_apply_merge(HullSmem<NT, M>& s, int t, int node, int half, int nL, int nR) {
+    if (nL <= 0 || nR <= 0) return;
+    int r0, keep_lo, keep_hi;
+    if (t < node + half) { r0 = s.cum[t] - s.cum[node]; keep_lo = 0; keep_hi = s.res_i[node]; }
+    else { r0 = s.cum[t] - s.cum[node + half]; keep_lo = s.res_j[node]; keep_hi = 1 << 30; }
+    const int l = s.lo[t], h = s.hi[t];
+    const int a = max(keep_lo - r0, 0), b = min(keep_hi - r0 + 1, h - l);
+    if (b <= a) { s.hi[t] = (uint16_t)l; }
+    else { s.lo[t] = (uint16_t)(l + a); s.hi[t] = (uint16_t)(l + b); }
+}
+
+template <int NT, int M, class Pts>
+__device__ __forceinline__ void ws_merge_node(HullSmem<NT, M>& s, const Pts& P, const SegConst& sc, int node, int half,
+                                              int c1, int nL, int nR) {
+    int flag = 0, is = nL - 1, js = 0;
+    if (nL > 0 && nR > 0) {
+        TileBridge<NT, M, Pts> br{s, P, sc, node, node + half, node + half, c1, nR - 1};
+        br.run(nL - 1, flag, is, js);
+        if (flag == 0) { is = nL - 1; js = 1; }
+    }
+    s.res_i[node] = is;
+    s.res_j[node] = js;
+}
+
+// Build the hull of points 0..n of a tile.  Thread t owns chunk t = points
+// [t*M, min((t+1)*M, n)] and runs the sequential monotone chain (the stack
+// form of pool-adjacent-violators) over it; chunk hulls are then merged up a
+// binary tree -- five warp-synchronous levels, then log2(NT/32) CTA levels.
+// A merge keeps a prefix of the left hull and a suffix of the right one
+// joined by their bridge (the divide-and-conquer step of Search Collisions,
+// Sec. 4.3 / Thm 4.2, as a tangent search), so every chunk only narrows the
+// surviving range [lo, hi) of its own list.  On return s.cum is the CTA
+// exclusive scan of the surviving counts and *total_vertices their sum.
+template <int NT, int M, class Pts>
+__device__ void ws_cta_hull(HullSmem<NT, M>& s, int n, const Pts& P, const SegConst& sc, int* total_vertices) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int cnt = 0;
+    {
+        const int first = t * M;
+        if (first < n) {
+            const int last = min(first + M, n);
+            int p0 = 0, p1 = 0;          // the two top entries of the stack
+            int64_t v0 = 0, v1 = 0;
+            for (int pnt = first; pnt <= last; ++pnt) {
+                const int64_t vp = P.v(pnt);
+                while (cnt >= 2 && !P.convex_v(p0, v0, p1, v1, pnt, vp, sc)) {
+                    --cnt;
+                    p1 = p0; v1 = v0;
+                    if (cnt >= 2) { p0 = s.H[(cnt - 2) * NT + t]; v0 = P.v(p0); }
+                }
+                s.H[cnt * NT + t] = (uint16_t)pnt;
+                p0 = p1; v0 = v1;
+                p1 = pnt; v1 = vp;
+                ++cnt;
+            }
+        }
+    }
+    s.lo[t] = 0;
+    s.hi[t] = (uint16_t)cnt;
+    __syncwarp();
+    // ---- warp levels: chunks of one warp, warp-relative ranks
+    for (int half = 1; half < 32; half <<= 1) {
+        const int c = (int)s.hi[t] - (int)s.lo[t];
+        const int inc = ws_warp_incl_scan<int>(c);
+        s.cum[t] = inc - c;
+        if (lane == 31) s.wtot[w] = inc;
+        __syncwarp();
+        const int mask = 2 * half - 1;
+        const int node = t & ~mask;
+        const int endR = ((node & 31) + 2 * half == 32) ? s.wtot[w] : s.cum[node + 2 * half];
+        const int nL = s.cum[node + half] - s.cum[node], nR = endR - s.cum[node + half];
+        if ((lane & mask) == 0) ws_merge_node<NT, M, Pts>(s, P, sc, node, half, node + 2 * half, nL, nR);
+        __syncwarp();
+        ws_apply_merge<NT, M>(s, t, node, half, nL, nR);
+        __syncwarp();
+    }
+    // ---- CTA levels
+    for (int half = 32; half < NT; half <<= 1) {
+        const int c = (int)s.hi[t] - (int)s.lo[t];
+        int tot;
+        const int ex = ws_block_excl_scan<NT, int>(c, s.wsum_i, &tot);
+        s.cum[t] = ex;
+        if (t == 0) s.cum[NT] = tot;
+        __syncthreads();
+        const int node = t - (t % (2 * half));
+        const int c1 = min(node + 2 * half, NT);
+        const int nL = s.cum[node + half] - s.cum[node];
+        const int nR = s.cum[c1] - s.cum[node + half];
+        if (t == node) ws_merge_node<NT, M, Pts>(s, P, sc, node, half, c1, nL, nR);
+        __syncthreads();
+        ws_apply_merge<NT, M>(s, t, node, half, nL, nR);
+        __syncthreads();
+    }
+    const int c = (int)s.hi[t] - (int)s.lo[t];
+    int tot;
+    const int ex = ws_block_excl_scan<NT, int>(c, s.wsum_i, &tot);
+    s.cum[t] = ex;
+    if (t == 0) s.cum[NT] = tot;
+    __syncthreads();
+    *total_vertices = tot;
 }
 
 // Bridge search between convex chains L (ranks 0..p) and R (ranks 0..q) that
@@ -221,84 +690,3 @@ __device__ __forceinline__ void ws_bridge(const GL& getL, int p, const GR& getR,
     istar = good; jstar = jgood;
 }
 
-// Build the hull of points 0..n.  XOf: functor p -> i128.  After return (and a
-// __syncthreads inside), s.lo/s.hi give each chunk's surviving vertices and
-// s.cum the exclusive scan of their counts (total = number of hull vertices).
-template <int NT, int M, class XOf>
-__device__ void ws_cta_hull(HullSmem<NT, M>& s, int n, const XOf& X, const SegConst& sc, int* total_vertices) {
-    const int t = threadIdx.x;
-    // 1. per-thread monotone chain over the chunk's points
-    int first = t * M;
-    int cnt = 0;
-    if (first < n) {
-        int last = min(first + M, n);
-        uint16_t* st = s.H + t * (M + 1);
-        for (int pnt = first; pnt <= last; ++pnt) {
-            i128 Xp = X(pnt);
-            while (cnt >= 2) {
-                int pa = st[cnt - 2], pb = st[cnt - 1];
-                if (ws_convex(X(pa), X(pb), Xp, pa, pb, pnt, sc)) break;
-                --cnt;
-            }
-            st[cnt++] = (uint16_t)pnt;
-        }
-    }
-    s.lo[t] = 0;
-    s.hi[t] = (uint16_t)cnt;
-    __syncthreads();
-    // 2. pairwise merges up the tree
-    for (int half = 1; half < NT; half <<= 1) {
-        int c = (int)s.hi[t] - (int)s.lo[t];
-        int tot;
-        int ex = ws_block_excl_scan<NT, int>(c, s.wsum_i, &tot);
-        s.cum[t] = ex;
-        if (t == 0) s.cum[NT] = tot;
-        __syncthreads();
-        if ((t % (2 * half)) == 0 && t + half < NT) {
-            int cL0 = t, cL1 = t + half, cR0 = t + half, cR1 = min(t + 2 * half, NT);
-            int nL = s.cum[cL1] - s.cum[cL0], nR = s.cum[cR1] - s.cum[cR0];
-            int flag = 0, is = 0, js = 0;
-            if (nL > 0 && nR > 0) {
-                auto getL = [&](int r, int64_t& pt, i128& Xv) {
-                    pt = ws_hull_point<NT, M>(s, cL0, cL1, r);
-                    Xv = X((int)pt);
-                };
-                auto getR = [&](int r, int64_t& pt, i128& Xv) {
-                    pt = ws_hull_point<NT, M>(s, cR0, cR1, r);
-                    Xv = X((int)pt);
-                };
-                ws_bridge(getL, nL - 1, getR, nR - 1, sc, flag, is, js);
-                if (flag == 0) { is = nL - 1; js = 1; }
-            } else {
-                is = nL - 1; js = 0;   // one side empty: nothing to merge
-            }
-            s.res_flag[t] = flag; s.res_i[t] = is; s.res_j[t] = js;
-        }
-        __syncthreads();
-        {
-            int node = t - (t % (2 * half));
-            if (node + half < NT) {
-                int nL = s.cum[node + half] - s.cum[node];
-                int nR = s.cum[min(node + 2 * half, NT)] - s.cum[node + half];
-                if (nL > 0 && nR > 0) {
-                    int r0, keep_lo, keep_hi;   // ranks of this chunk and the kept rank window
-                    if (t < node + half) { r0 = s.cum[t] - s.cum[node]; keep_lo = 0; keep_hi = s.res_i[node]; }
-                    else { r0 = s.cum[t] - s.cum[node + half]; keep_lo = s.res_j[node]; keep_hi = 1 << 30; }
-                    int l = s.lo[t], h = s.hi[t];
-                    int cntc = h - l;
-                    int a = max(keep_lo - r0, 0), b = min(keep_hi - r0 + 1, cntc);
-                    if (b <= a) { s.lo[t] = (uint16_t)l; s.hi[t] = (uint16_t)l; }
-                    else { s.lo[t] = (uint16_t)(l + a); s.hi[t] = (uint16_t)(l + b); }
-                }
-            }
-        }
-        __syncthreads();
-    }
-    int c = (int)s.hi[t] - (int)s.lo[t];
-    int tot;
-    int ex = ws_block_excl_scan<NT, int>(c, s.wsum_i, &tot);
-    s.cum[t] = ex;
-    if (t == 0) s.cum[NT] = tot;
-    __syncthreads();
-    *total_vertices = tot;
-}

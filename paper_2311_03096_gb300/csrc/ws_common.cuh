@@ -128,6 +128,20 @@ __device__ __forceinline__ void ws_split_lambda(double lam, uint64_t& mlam, int&
     if (m == 0) elam = 0;
 }
 
+// Constants for fixed-point scale 2^L (q = x * 2^L).
+__device__ __forceinline__ SegConst ws_seg_const_L(int64_t d, double lam, int L) {
+    SegConst c;
+    c.d = d;
+    c.L = L;
+    int elam;
+    ws_split_lambda(lam, c.mlam, elam);
+    c.s = elam + c.L;
+    c.dm1 = d > 1 ? (uint64_t)(d - 1) : 1ull;
+    c.mu_d = d > 1 ? lam / (double)(d - 1) : 0.0;
+    c.mu_f = (float)c.mu_d;
+    return c;
+}
+
 template <typename T>
 __device__ __forceinline__ SegConst ws_seg_const(int64_t d, double lam, int emax) {
     SegConst c;

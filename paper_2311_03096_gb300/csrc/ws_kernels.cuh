@@ -35,9 +35,10 @@ struct WsProf {
     do { (PROF)->begin((ST), (KIND)); __VA_ARGS__; (PROF)->end((ST)); } while (0)
 
 // Large-path tile geometry.
-constexpr int WS_SORT_NT = 512;              // threads per onesweep CTA
+constexpr int WS_SORT_NT = 256;              // threads per onesweep CTA
 constexpr int WS_SORT_ITEMS = 16;            // keys per thread
-constexpr int WS_SORT_TILE = WS_SORT_NT * WS_SORT_ITEMS;   // 8192 keys per sort tile
+constexpr int WS_SORT_CHAINS = 1;            // independent ranking chains per warp
+constexpr int WS_SORT_TILE = WS_SORT_NT * WS_SORT_ITEMS;   // 4096 keys per sort tile
 constexpr int WS_HULL_NT = 256;              // threads per hull-tile CTA
 constexpr int WS_HULL_M = 16;                // points per thread chunk
 constexpr int WS_HULL_TILE = WS_HULL_NT * WS_HULL_M;       // 4096 elements per hull tile
@@ -118,6 +119,7 @@ struct LargeWork {
     uint32_t* hist;          // [n_lseg][passes][256]
     uint64_t* lookback;      // [passes][n_sort_tiles][256]
     uint32_t* tile_counter;  // [passes]
+    uint32_t* epoch;         // [1] look-back epoch, advanced by every sort
     // hull
     uint16_t* vp;            // [n_hull_tiles][WS_HULL_TILE + 1] vertex points (tile-local)
     i128* vx;                // [n_hull_tiles][WS_HULL_TILE + 1] X at vertices (tile-local)

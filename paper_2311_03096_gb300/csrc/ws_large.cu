@@ -22,10 +22,12 @@ constexpr int HM = WS_HULL_M;
 // 1. per-tile hull
 // ---------------------------------------------------------------------------
 struct TileHullSmem {
-    int64_t loc[HT + 1];
-    i128 base[HNT + 1];
+    TilePrefix<HNT, HM> pre;
     HullSmem<HNT, HM> hull;
-    i128 wsum128[HNT / 32];
+    SegConst sc;     // global fixed-point scale of the segment
+    SegConst sct;    // scale of this tile when it lies in one binade
+    float muq, muqt;
+    int fast, fastt;
 };
 
 template <typename T>
@@ -36,6 +38,7 @@ __global__ void __launch_bounds__(HNT) k_tile_hull(const typename KeyOf<T>::K* _
                                                    uint16_t* vp, i128* vx, int32_t* nvert, i128* tile_total,
                                                    Piece* pieces, int32_t* npieces, uint32_t* status) {
     typedef KeyOf<T> KO;
+    typedef typename KO::K K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileHullSmem& s = *reinterpret_cast<TileHullSmem*>(smem_raw);
     const int t = threadIdx.x;
@@ -43,37 +46,66 @@ __global__ void __launch_bounds__(HNT) k_tile_hull(const typename KeyOf<T>::K* _
     const TileDesc td = htiles[tile];
     const LargeSeg ls = lsegs[td.lseg];
     const double lam = lambdas[ls.seg];
-    if (!(lam >= 0.0) || !(lam <= 1.7976931348623157e308)) {
-        if (t == 0) ws_flag(status, WS_STATUS_BAD_LAMBDA);
-    }
-    const double lamv = (lam >= 0.0 && lam <= 1.7976931348623157e308) ? lam : 0.0;
+    const bool lam_ok = lam >= 0.0 && lam <= 1.7976931348623157e308;
+    const double lamv = lam_ok ? lam : 0.0;
+    const int n = td.len;
+    const K* kp = sorted + td.kpos;
+    const K kfirst = kp[0], klast = kp[n - 1];
     const T xlo = KO::from_key(sorted[ls.kpos]), xhi = KO::from_key(sorted[ls.kpos + ls.len - 1]);
     const int emax = max(ws_eff_exp(xlo), ws_eff_exp(xhi));
-    if (td.tin == 0 && t == 0) rt[td.lseg].emax = emax;
-    const SegConst sc = ws_seg_const<T>(ls.len, lamv, emax);
-    const int n = td.len;
-    const typename KO::K* kp = sorted + td.kpos;
-    int64_t run = 0;
-    for (int i = 0; i < HM; ++i) {
-        int p = t * HM + i;
-        if (p <= n) s.loc[p] = run;
-        if (p < n) run += ws_fixed<T>(KO::from_key(kp[p]), emax);
+    if (t == 0) {
+        if (!lam_ok) ws_flag(status, WS_STATUS_BAD_LAMBDA);
+        if (td.tin == 0) rt[td.lseg].emax = emax;
+        s.sc = ws_seg_const<T>(ls.len, lamv, emax);
+        bool f;
+        s.muq = ws_muq(lamv, s.sc, f);
+        s.fast = f ? 1 : 0;
+        const int sh = ws_eff_exp(KO::from_key(kfirst)) - emax + KO::FIX_OFS;
+        s.sct = ws_seg_const_L(ls.len, lamv, s.sc.L - (sh > 0 ? sh : 0));
+        s.muqt = ws_muq(lamv, s.sct, f);
+        s.fastt = f ? 1 : 0;
     }
-    i128 total;
-    i128 ex = ws_block_excl_scan<HNT, i128>((i128)run, s.wsum128, &total);
-    s.base[t] = ex;
-    if (t == 0) { s.base[HNT] = total; if (n == HT) s.loc[HT] = 0; }
-    __syncthreads();
-    auto X = [&](int p) -> i128 { return s.base[p / HM] + (i128)s.loc[p]; };
-    int nv;
-    ws_cta_hull<HNT, HM>(s.hull, n, X, sc, &nv);
+    // this thread's 16 consecutive sorted keys (vector loads when whole and aligned)
+    K kr[HM];
     {
-        int l = s.hull.lo[t], h = s.hull.hi[t], o = s.hull.cum[t];
-        size_t b = (size_t)tile * (HT + 1);
+        const int first = t * HM;
+        const K* src = kp + first;
+        if (first + HM <= n && (((uintptr_t)src) & 15) == 0) {
+            constexpr int NV = HM * (int)sizeof(K) / 16;
+            const uint4* v4 = reinterpret_cast<const uint4*>(src);
+            uint4 buf[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) buf[i] = v4[i];
+            const K* bk = reinterpret_cast<const K*>(buf);
+#pragma unroll
+            for (int i = 0; i < HM; ++i) kr[i] = bk[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < HM; ++i) kr[i] = (first + i < n) ? src[i] : (K)0;
+        }
+    }
+    int64_t q0;
+    i128 total;
+    int bsh;
+    const int mode = ws_tile_prefix<T, HNT, HM>(s.pre, kr, kfirst, klast, n, emax, q0, total, bsh);
+    int nv;
+    if (mode == WS_TILE_BINADE) {
+        const TilePtsBinade<HM> P{s.pre.s64, s.muqt, s.fastt != 0};
+        ws_cta_hull<HNT, HM>(s.hull, n, P, s.sct, &nv);
+    } else if (mode == WS_TILE_NARROW) {
+        const TilePts<HM, true> P{s.pre.s64, s.pre.base, q0, s.muq, s.fast != 0};
+        ws_cta_hull<HNT, HM>(s.hull, n, P, s.sc, &nv);
+    } else {
+        const TilePts<HM, false> P{s.pre.s64, s.pre.base, q0, 0.0f, false};
+        ws_cta_hull<HNT, HM>(s.hull, n, P, s.sc, &nv);
+    }
+    {
+        const int l = s.hull.lo[t], h = s.hull.hi[t], o = s.hull.cum[t];
+        const size_t b = (size_t)tile * (HT + 1);
         for (int i = l; i < h; ++i) {
-            int pnt = s.hull.H[t * (HM + 1) + i];
+            const int pnt = s.hull.H[i * HNT + t];
             vp[b + o + (i - l)] = (uint16_t)pnt;
-            vx[b + o + (i - l)] = X(pnt);
+            vx[b + o + (i - l)] = ws_tile_X<HM>(s.pre.s64, s.pre.base, mode, q0, bsh, pnt);
         }
     }
     if (t == 0) {

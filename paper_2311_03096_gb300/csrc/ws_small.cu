@@ -13,8 +13,7 @@ struct SmallSmem {
     static constexpr int CAP = NT * M;
     K keys[CAP];
     uint16_t idx[CAP];
-    int64_t loc[CAP + 1];   // prefix of q inside the point's chunk
-    i128 base[NT + 1];      // prefix of q at each chunk start
+    TilePrefix<NT, M> pre;  // fixed-point prefix sums of the sorted segment
     HullSmem<NT, M> hull;
     uint16_t V[CAP + 1];    // hull vertices (points)
     union {
@@ -27,9 +26,11 @@ struct SmallSmem {
             uint8_t mark[CAP];
         } out;
     } u;
-    i128 wsum128[NT / 32];
     int wsum_i[NT / 32];
     int flags;
+    SegConst sc, sct;
+    float muq, muqt;
+    int fast, fastt;
 };
 
 template <typename T, int NT, int M>
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
             dg[k] = (uint32_t)((kk[k] >> (8 * pass)) & 0xff);
         }
         __syncthreads();
-        ws_rank_digits<NT, ITEMS>(dg, valid, pos, s.u.sort.whist, s.u.sort.dcount, s.u.sort.dstart, nullptr);
+        ws_rank_digits<NT, ITEMS, 1>(dg, valid, pos, s.u.sort.whist, s.u.sort.dcount, s.u.sort.dstart);
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k)
             if (valid[k]) { s.keys[pos[k]] = kk[k]; s.idx[pos[k]] = ii[k]; }
@@ -115,31 +116,44 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
     // ---- fixed point and prefix sums (blocked: thread t owns sorted [t*M, t*M+M))
     const T xlo = KO::from_key(s.keys[0]), xhi = KO::from_key(s.keys[n - 1]);
     const int emax = max(ws_eff_exp(xlo), ws_eff_exp(xhi));
-    const SegConst sc = ws_seg_const<T>(n, lam, emax);
-    i128 csum = 0;
-    {
-        int first = t * M;
-        int64_t run = 0;
-        for (int i = 0; i < M; ++i) {
-            int p = first + i;
-            if (p <= n) s.loc[p] = run;
-            if (p < n) run += ws_fixed<T>(KO::from_key(s.keys[p]), emax);
-        }
-        csum = (i128)run;
+    if (t == 0) {
+        s.sc = ws_seg_const<T>(n, lam, emax);
+        bool f;
+        s.muq = ws_muq(lam, s.sc, f);
+        s.fast = f ? 1 : 0;
     }
+    int64_t q0;
     i128 total;
-    i128 ex = ws_block_excl_scan<NT, i128>(csum, s.wsum128, &total);
-    s.base[t] = ex;
-    if (t == 0) { s.base[NT] = total; if (n == CAP) s.loc[CAP] = 0; }
-    __syncthreads();
-    auto X = [&](int p) -> i128 { return s.base[p / M] + (i128)s.loc[p]; };
+    int bsh;
+    K kr[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) kr[i] = (t * M + i < n) ? s.keys[t * M + i] : (K)0;
+    if (t == 0) {
+        const int sh0 = ws_eff_exp(KO::from_key(s.keys[0])) - emax + KO::FIX_OFS;
+        s.sct = ws_seg_const_L(n, lam, s.sc.L - (sh0 > 0 ? sh0 : 0));
+        bool f;
+        s.muqt = ws_muq(lam, s.sct, f);
+        s.fastt = f ? 1 : 0;
+    }
+    const int mode = ws_tile_prefix<T, NT, M>(s.pre, kr, s.keys[0], s.keys[n - 1], n, emax, q0, total, bsh);
+    const SegConst& sc = s.sc;
 
     // ---- exact hull (in-CTA merge)
     int nv;
-    ws_cta_hull<NT, M>(s.hull, n, X, sc, &nv);
+    if (mode == WS_TILE_BINADE) {
+        const TilePtsBinade<M> P{s.pre.s64, s.muqt, s.fastt != 0};
+        ws_cta_hull<NT, M>(s.hull, n, P, s.sct, &nv);
+    } else if (mode == WS_TILE_NARROW) {
+        const TilePts<M, true> P{s.pre.s64, s.pre.base, q0, s.muq, s.fast != 0};
+        ws_cta_hull<NT, M>(s.hull, n, P, sc, &nv);
+    } else {
+        const TilePts<M, false> P{s.pre.s64, s.pre.base, q0, 0.0f, false};
+        ws_cta_hull<NT, M>(s.hull, n, P, sc, &nv);
+    }
+    auto X = [&](int p) -> i128 { return ws_tile_X<M>(s.pre.s64, s.pre.base, mode, q0, bsh, p); };
     {
         int l = s.hull.lo[t], h = s.hull.hi[t], o = s.hull.cum[t];
-        for (int i = l; i < h; ++i) s.V[o + (i - l)] = s.hull.H[t * (M + 1) + i];
+        for (int i = l; i < h; ++i) s.V[o + (i - l)] = s.hull.H[i * NT + t];
     }
     for (int p = t; p < n; p += NT) s.u.out.mark[p] = 0;
     __syncthreads();

@@ -8,16 +8,24 @@
 //
 // One histogram pass computes every digit histogram of every large segment;
 // then each 8-bit digit pass is a single "onesweep" kernel: a CTA ranks its
-// 8192 keys by digit in shared memory, publishes its per-digit counts, gets
+// 4096 keys by digit in shared memory, publishes its per-digit counts, gets
 // the counts of the earlier tiles of the same segment through a decoupled
 // look-back (bounded waits), and writes its keys as per-digit contiguous runs.
 #include "ws_kernels.cuh"
 
 namespace {
 
+// Look-back word: [63:62] status (1 = tile aggregate, 2 = inclusive prefix),
+// [61:40] epoch of the call that wrote it, [39:0] count.  Every call uses a
+// new epoch (incremented on the device, so CUDA-graph replays also advance
+// it), which makes the words of the previous call read as "not ready"
+// without clearing the array.
 constexpr uint64_t LB_AGG = 1ull << 62;
 constexpr uint64_t LB_INC = 2ull << 62;
-constexpr uint64_t LB_CNT = (1ull << 62) - 1ull;
+constexpr uint64_t LB_STATUS = 3ull << 62;
+constexpr int LB_EPOCH_SHIFT = 40;
+constexpr uint64_t LB_EPOCH_MASK = ((1ull << 22) - 1ull) << LB_EPOCH_SHIFT;
+constexpr uint64_t LB_CNT = (1ull << LB_EPOCH_SHIFT) - 1ull;
 
 __device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -53,8 +61,9 @@ __global__ void __launch_bounds__(WS_SORT_NT) k_hist(const T* __restrict__ value
 }
 
 // exclusive scan of every (segment, pass) histogram, in place
-__global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist) {
+__global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist, uint32_t* epoch) {
     __shared__ uint32_t ws[8];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *epoch = (*epoch + 1u) & ((1u << 22) - 1u);
     uint32_t* h = hist + (size_t)blockIdx.x * 256;
     uint32_t v = h[threadIdx.x];
     uint32_t tot;
@@ -63,14 +72,14 @@ __global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist) {
 }
 
 template <typename T, bool FIRST>
-__global__ void __launch_bounds__(WS_SORT_NT) k_onesweep(const T* __restrict__ values,
-                                                         const typename KeyOf<T>::K* __restrict__ keys_in,
-                                                         typename KeyOf<T>::K* __restrict__ keys_out,
-                                                         const TileDesc* __restrict__ tiles,
-                                                         const LargeSeg* __restrict__ lsegs,
-                                                         const uint32_t* __restrict__ hist, uint64_t* lookback,
-                                                         uint32_t* counter, int pass, uint32_t* status,
-                                                         uint64_t spin_limit) {
+__global__ void __launch_bounds__(WS_SORT_NT, 4) k_onesweep(const T* __restrict__ values,
+                                                            const typename KeyOf<T>::K* __restrict__ keys_in,
+                                                            typename KeyOf<T>::K* __restrict__ keys_out,
+                                                            const TileDesc* __restrict__ tiles,
+                                                            const LargeSeg* __restrict__ lsegs,
+                                                            const uint32_t* __restrict__ hist, uint64_t* lookback,
+                                                            uint32_t* counter, const uint32_t* __restrict__ epoch_p,
+                                                            int pass, uint32_t* status, uint64_t spin_limit) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     constexpr int P = KO::BITS / 8;
@@ -78,9 +87,10 @@ __global__ void __launch_bounds__(WS_SORT_NT) k_onesweep(const T* __restrict__ v
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K* skeys = reinterpret_cast<K*>(smem_raw);
     uint32_t* whist = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * TILE);
-    uint32_t* dcount = whist + (NT / 32) * 256;
+    uint32_t* dcount = whist + (NT / 32) * WS_SORT_CHAINS * 256;
     uint32_t* dstart = dcount + 256;
-    uint32_t* excl = dstart + 256;
+    int64_t* gbase = reinterpret_cast<int64_t*>(dstart + 256);
+    __shared__ uint32_t ecount[256];
     __shared__ int s_tile;
     __shared__ int s_timeout;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -90,60 +100,88 @@ __global__ void __launch_bounds__(WS_SORT_NT) k_onesweep(const T* __restrict__ v
     const TileDesc td = tiles[tile];
     const int64_t seg_k = lsegs[td.lseg].kpos;
     const uint32_t* dbase = hist + ((size_t)td.lseg * P + pass) * 256;
+    const uint64_t ep = (uint64_t)(*epoch_p) << LB_EPOCH_SHIFT;
+    const int shift = 8 * pass;
 
     K key[ITEMS];
-    uint32_t dg[ITEMS];
-    bool valid[ITEMS];
     int pos[ITEMS];
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-        int p = w * 32 * ITEMS + k * 32 + lane;
-        valid[k] = p < td.len;
-        if (FIRST) key[k] = valid[k] ? KO::to_key(values[td.vpos + p]) : (K)0;
-        else key[k] = valid[k] ? keys_in[td.kpos + p] : (K)0;
-        dg[k] = (uint32_t)((key[k] >> (8 * pass)) & 0xff);
-    }
-    ws_rank_digits<NT, ITEMS>(dg, valid, pos, whist, dcount, dstart, nullptr);
-
-    // publish this tile's per-digit counts, then look back over earlier tiles
     uint64_t* my_lb = lookback + (size_t)tile * 256;
+    {
+        uint32_t dg[ITEMS];
+        bool valid[ITEMS];
+        const int base = w * 32 * ITEMS + lane;
+        if (t < 256) ecount[t] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int p = base + k * 32;
+            valid[k] = p < td.len;
+            if (FIRST) key[k] = valid[k] ? KO::to_key(values[td.vpos + p]) : (K)0;
+            else key[k] = valid[k] ? keys_in[td.kpos + p] : (K)0;
+            dg[k] = (uint32_t)((key[k] >> shift) & 0xff);
+            if (valid[k]) atomicAdd(&ecount[dg[k]], 1u);
+        }
+        __syncthreads();
+        // publish this tile's per-digit counts before the (longer) ranking, so
+        // that later tiles' look-backs do not wait for it
+        if (t < 256) st_relaxed_u64(&my_lb[t], (td.tin == 0 ? LB_INC : LB_AGG) | ep | (uint64_t)ecount[t]);
+        ws_rank_digits<NT, ITEMS, WS_SORT_CHAINS>(dg, valid, pos, whist, dcount, dstart);
+    }
+
+    // look back over earlier tiles of the segment (windows of 4 predecessors
+    // per round trip)
     if (t < 256) {
-        uint64_t c = dcount[t];
+        const uint64_t c = dcount[t];
+        int64_t gb;   // global position of this digit's first key of the tile, minus its local start
         if (td.tin == 0) {
-            st_relaxed_u64(&my_lb[t], LB_INC | c);
-            excl[t] = 0;
+            gb = 0;
         } else {
-            st_relaxed_u64(&my_lb[t], LB_AGG | c);
             uint64_t run = 0;
             int j = tile - 1;
             uint64_t it = 0;
-            while (true) {
-                uint64_t v = ld_relaxed_u64(&lookback[(size_t)j * 256 + t]);
-                uint64_t f = v & ~LB_CNT;
-                if (f == 0) {
-                    if (++it > spin_limit) { s_timeout = 1; break; }
-                    ws_backoff((int)min(it, (uint64_t)1 << 20));
-                    continue;
+            bool done = false;
+            while (!done) {
+                constexpr int WIN = 4;
+                uint64_t v[WIN];
+                const int nwin = min(WIN, j - td.first + 1);
+#pragma unroll
+                for (int u = 0; u < WIN; ++u)
+                    if (u < nwin) v[u] = ld_relaxed_u64(&lookback[(size_t)(j - u) * 256 + t]);
+                int u = 0;
+                for (; u < nwin; ++u) {
+                    uint64_t x = v[u];
+                    while ((x & LB_STATUS) == 0 || (x & LB_EPOCH_MASK) != ep) {
+                        if (++it > spin_limit) { s_timeout = 1; break; }
+                        ws_backoff((int)min(it, (uint64_t)1 << 20));
+                        x = ld_relaxed_u64(&lookback[(size_t)(j - u) * 256 + t]);
+                    }
+                    if ((x & LB_STATUS) == 0 || (x & LB_EPOCH_MASK) != ep) { done = true; break; }   // gave up
+                    run += x & LB_CNT;
+                    if ((x & LB_STATUS) == LB_INC || j - u <= td.first) { done = true; break; }
                 }
-                run += v & LB_CNT;
-                if (f == LB_INC || j <= td.first) break;
-                --j;
+                if (!done) j -= nwin;
             }
-            excl[t] = (uint32_t)run;
-            st_relaxed_u64(&my_lb[t], LB_INC | (run + c));
+            st_relaxed_u64(&my_lb[t], LB_INC | ep | (run + c));
+            gb = (int64_t)run;
         }
+        gbase[t] = seg_k + (int64_t)dbase[t] + gb - (int64_t)dstart[t];
     }
     // stage the tile in digit order
+    {
+        const int base = w * 32 * ITEMS + lane;
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k)
-        if (valid[k]) skeys[pos[k]] = key[k];
+        for (int k = 0; k < ITEMS; ++k)
+            if (base + k * 32 < td.len) skeys[pos[k]] = key[k];
+    }
     __syncthreads();
     if (t == 0 && s_timeout) ws_flag(status, WS_STATUS_TIMEOUT);
-    for (int j = t; j < td.len; j += NT) {
-        K kk = skeys[j];
-        uint32_t d = (uint32_t)((kk >> (8 * pass)) & 0xff);
-        int64_t dst = seg_k + (int64_t)dbase[d] + (int64_t)excl[d] + (int64_t)(j - (int)dstart[d]);
-        keys_out[dst] = kk;
+#pragma unroll 4
+    for (int k = 0; k < ITEMS; ++k) {
+        const int j = t + k * NT;
+        if (j < td.len) {
+            const K kk = skeys[j];
+            keys_out[gbase[(uint32_t)((kk >> shift) & 0xff)] + j] = kk;
+        }
     }
 }
 
@@ -152,7 +190,8 @@ __global__ void __launch_bounds__(WS_SORT_NT) k_onesweep(const T* __restrict__ v
 template <typename T>
 size_t ws_onesweep_smem() {
     typedef typename KeyOf<T>::K K;
-    return sizeof(K) * WS_SORT_TILE + sizeof(uint32_t) * ((WS_SORT_NT / 32) * 256 + 3 * 256);
+    return sizeof(K) * WS_SORT_TILE + sizeof(uint32_t) * ((WS_SORT_NT / 32) * WS_SORT_CHAINS * 256 + 2 * 256) +
+           sizeof(int64_t) * 256;
 }
 
 template <typename T>
@@ -165,12 +204,10 @@ cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* stat
     if (W.n_sort_tiles == 0) return cudaSuccess;
     e = cudaMemsetAsync(W.hist, 0, sizeof(uint32_t) * (size_t)W.n_lseg * P * 256, st);
     if (e) return e;
-    e = cudaMemsetAsync(W.lookback, 0, sizeof(uint64_t) * (size_t)P * W.n_sort_tiles * 256, st);
-    if (e) return e;
     e = cudaMemsetAsync(W.tile_counter, 0, sizeof(uint32_t) * P, st);
     if (e) return e;
     WS_LAUNCH(W.prof, WSK_HIST, st, (k_hist<T><<<W.n_sort_tiles, WS_SORT_NT, 0, st>>>(values, W.sort_tiles, W.hist, status)));
-    WS_LAUNCH(W.prof, WSK_HIST_SCAN, st, (k_hist_scan<<<W.n_lseg * P, 256, 0, st>>>(W.hist)));
+    WS_LAUNCH(W.prof, WSK_HIST_SCAN, st, (k_hist_scan<<<W.n_lseg * P, 256, 0, st>>>(W.hist, W.epoch)));
     size_t smem = ws_onesweep_smem<T>();
     e = cudaFuncSetAttribute(k_onesweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
@@ -182,10 +219,12 @@ cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* stat
         uint64_t* lb = W.lookback + (size_t)p * W.n_sort_tiles * 256;
         if (p == 0)
             WS_LAUNCH(W.prof, WSK_ONESWEEP, st, (k_onesweep<T, true><<<W.n_sort_tiles, WS_SORT_NT, smem, st>>>(
-                values, nullptr, dst, W.sort_tiles, W.lsegs, W.hist, lb, W.tile_counter + p, p, status, spin_limit)));
+                values, nullptr, dst, W.sort_tiles, W.lsegs, W.hist, lb, W.tile_counter + p, W.epoch, p, status,
+                spin_limit)));
         else
             WS_LAUNCH(W.prof, WSK_ONESWEEP, st, (k_onesweep<T, false><<<W.n_sort_tiles, WS_SORT_NT, smem, st>>>(
-                values, src, dst, W.sort_tiles, W.lsegs, W.hist, lb, W.tile_counter + p, p, status, spin_limit)));
+                values, src, dst, W.sort_tiles, W.lsegs, W.hist, lb, W.tile_counter + p, W.epoch, p, status,
+                spin_limit)));
         K* tmp = src; src = dst; dst = tmp;
     }
     *sorted = src;   // the buffer written last
