@@ -70,7 +70,7 @@ struct ws_plan {
     int32_t* tile_piece = nullptr;
     SegRuntime* rt = nullptr;
     void* table = nullptr;
-    int32_t* dir = nullptr;
+    DirEntry* dir = nullptr;
     void* bsum = nullptr;
     int32_t* bcnt = nullptr;
 };
@@ -171,7 +171,7 @@ ws_status build_plan(ws_plan* p) {
             htiles.push_back(td);
         }
         ls.hull_count = (int32_t)htiles.size() - ls.hull_first;
-        ls.dir_cap_log2 = ceil_log2(len);
+        ls.dir_cap_log2 = std::min(ceil_log2(len), WS_DIR_MAX_LOG2);
         ls.dir_pos = dir_pos;
         dir_pos += ((int64_t)1 << ls.dir_cap_log2) + 1;
         kpos += (len + 3) & ~(int64_t)3;   // keep every segment's keys 16-byte aligned
@@ -238,7 +238,7 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->tile_piece, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->rt, sizeof(SegRuntime) * p->n_lseg))) return st;
     if ((st = plan_alloc(p, &p->table, (f64 ? sizeof(CEntry<double>) : sizeof(CEntry<float>)) * slots))) return st;
-    if ((st = plan_alloc(p, (void**)&p->dir, sizeof(int32_t) * (size_t)dir_pos))) return st;
+    if ((st = plan_alloc(p, (void**)&p->dir, sizeof(DirEntry) * (size_t)dir_pos))) return st;
     if ((st = plan_alloc(p, &p->bsum, vsize * slots))) return st;
     if ((st = plan_alloc(p, (void**)&p->bcnt, sizeof(int32_t) * slots))) return st;
     if (cudaMemset(p->rt, 0, sizeof(SegRuntime) * p->n_lseg) != cudaSuccess) return WS_ERR_CUDA;

@@ -88,6 +88,14 @@ template <typename T> struct CEntry;
 template <> struct CEntry<float> { uint32_t key; float val; };
 template <> struct CEntry<double> { uint64_t key; double val; };
 
+// Directory entry: first cluster whose start falls in the bucket (or in a
+// later one) and the top 32 bits of that cluster's start key.
+struct DirEntry {
+    int32_t idx;
+    uint32_t key32;
+};
+constexpr int WS_DIR_MAX_LOG2 = 22;   // <= 2^22 buckets per segment (32 MiB: stays in L2)
+
 // Per-segment run-time values computed on the device.
 struct SegRuntime {
     int64_t n_clusters;
@@ -131,7 +139,7 @@ struct LargeWork {
     int32_t* tile_piece;     // [n_hull_tiles] piece index in the root list or -1
     SegRuntime* rt;          // [n_lseg]
     CEntry<T>* table;        // [n_keys + n_lseg]
-    int32_t* dir;            // directory slices
+    DirEntry* dir;           // directory slices
     // backward
     T* bsum;                 // [n_keys + n_lseg]
     int32_t* bcnt;           // [n_keys + n_lseg]

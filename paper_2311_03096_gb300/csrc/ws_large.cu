@@ -167,6 +167,71 @@ struct NodeView {
     }
 };
 
+// Bridge between two node hulls by walking outward from their junction
+// (the linear merge of two convex chains), stepping through the piece lists
+// directly.  Returns false (no result) after too many steps; the caller then
+// runs the galloping search.  Same outputs as ws_bridge.
+__device__ __forceinline__ void ws_piece_vertex(const Piece* P, int pi, int v, const uint16_t* vp, const i128* vx,
+                                                const i128* toff, int hull_first, int64_t& pt, i128& X) {
+    const Piece q = P[pi];
+    const size_t idx = (size_t)q.tile * (HT + 1) + v;
+    pt = (int64_t)(q.tile - hull_first) * HT + vp[idx];
+    X = toff[q.tile] + vx[idx];
+}
+
+__device__ bool ws_bridge_walk(const Piece* PL, int npL, const Piece* PR, int npR, const uint16_t* vp,
+                               const i128* vx, const i128* toff, int hull_first, const SegConst& sc, int& flag,
+                               int& istar, int& jstar) {
+    // cursors: (piece, vertex index in the tile list)
+    int lp = npL - 1, lv = PL[lp].hi - 1;   // L_p = junction
+    int rp = 0, rv = PR[0].lo;              // R_0 = junction
+    auto prevL = [&](int& p, int& v) -> bool {
+        if (v > PL[p].lo) { --v; return true; }
+        if (p == 0) return false;
+        --p; v = PL[p].hi - 1; return true;
+    };
+    auto nextR = [&](int& p, int& v) -> bool {
+        if (v + 1 < PR[p].hi) { ++v; return true; }
+        if (p + 1 >= npR) return false;
+        ++p; v = PR[p].lo; return true;
+    };
+    int64_t pj; i128 Xj;
+    ws_piece_vertex(PR, rp, rv, vp, vx, toff, hull_first, pj, Xj);
+    if (!prevL(lp, lv) || !nextR(rp, rv)) { flag = 0; return true; }   // a one-vertex side: nothing to merge
+    int64_t pl, pr; i128 Xl, Xr;
+    ws_piece_vertex(PL, lp, lv, vp, vx, toff, hull_first, pl, Xl);
+    ws_piece_vertex(PR, rp, rv, vp, vx, toff, hull_first, pr, Xr);
+    if (ws_convex(Xl, Xj, Xr, pl, pj, pr, sc)) { flag = 0; return true; }
+    flag = 1;
+    int steps = 0;
+    constexpr int WALK_MAX = 32;
+    while (true) {
+        bool moved = false;
+        while (true) {
+            int p2 = lp, v2 = lv;
+            if (!prevL(p2, v2)) break;
+            int64_t pm; i128 Xm;
+            ws_piece_vertex(PL, p2, v2, vp, vx, toff, hull_first, pm, Xm);
+            if (ws_convex(Xm, Xl, Xr, pm, pl, pr, sc)) break;
+            lp = p2; lv = v2; pl = pm; Xl = Xm; moved = true;
+            if (++steps > WALK_MAX) return false;
+        }
+        while (true) {
+            int p2 = rp, v2 = rv;
+            if (!nextR(p2, v2)) break;
+            int64_t pn; i128 Xn;
+            ws_piece_vertex(PR, p2, v2, vp, vx, toff, hull_first, pn, Xn);
+            if (ws_convex(Xl, Xr, Xn, pl, pr, pn, sc)) break;
+            rp = p2; rv = v2; pr = pn; Xr = Xn; moved = true;
+            if (++steps > WALK_MAX) return false;
+        }
+        if (!moved) break;
+    }
+    istar = PL[lp].cum + (lv - PL[lp].lo);
+    jstar = PR[rp].cum + (rv - PR[rp].lo);
+    return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_merge(const MergeNode* __restrict__ nodes, const LargeSeg* __restrict__ lsegs,
                                                const double* __restrict__ lambdas, const SegRuntime* __restrict__ rt,
@@ -190,9 +255,11 @@ __global__ void __launch_bounds__(256) k_merge(const MergeNode* __restrict__ nod
         int nL = L.count(), nR = R.count();
         int flag = 0, is = nL - 1, js = 0;
         if (nL > 0 && nR > 0) {
-            auto gl = [&](int r, int64_t& pt, i128& X) { L.get(r, pt, X); };
-            auto gr = [&](int r, int64_t& pt, i128& X) { R.get(r, pt, X); };
-            ws_bridge(gl, nL - 1, gr, nR - 1, sc, flag, is, js);
+            if (!ws_bridge_walk(PL, npL, PR, npR, vp, vx, toff, ls.hull_first, sc, flag, is, js)) {
+                auto gl = [&](int r, int64_t& pt, i128& X) { L.get(r, pt, X); };
+                auto gr = [&](int r, int64_t& pt, i128& X) { R.get(r, pt, X); };
+                ws_bridge(gl, nL - 1, gr, nR - 1, sc, flag, is, js);
+            }
             if (flag == 0) { is = nL - 1; js = 1; }
         }
         // pieces holding istar and jstar
@@ -292,7 +359,7 @@ __device__ __forceinline__ int ws_bucket(float x, float lo, float scale, int nb)
 // ---------------------------------------------------------------------------
 constexpr int GAP_INLINE = 64;
 
-struct BigGap { int64_t pos; int32_t count; int32_t value; };
+struct BigGap { int64_t pos; int32_t count; int32_t value; uint32_t key32; int32_t pad; };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htiles, const LargeSeg* __restrict__ lsegs,
@@ -302,7 +369,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
                                                const i128* __restrict__ toff, const Piece* __restrict__ pieces,
                                                const int32_t* __restrict__ npieces,
                                                const int32_t* __restrict__ tile_piece, CEntry<T>* table,
-                                               int32_t* dir, BigGap* gaps, uint32_t* ngaps, int64_t gap_cap,
+                                               DirEntry* dir, BigGap* gaps, uint32_t* ngaps, int64_t gap_cap,
                                                int fp64, uint32_t* status) {
     typedef KeyOf<T> KO;
     const int tile = blockIdx.x;
@@ -318,7 +385,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
     const int np = npieces[ls.hull_first];
     const Piece pc = P[tp];
     const int nb = 1 << R.dir_log2;
-    int32_t* D = dir + ls.dir_pos;
+    DirEntry* D = dir + ls.dir_pos;
     auto vertex = [&](int piece_idx, int i, int64_t& pt, i128& X) {
         const Piece q = P[piece_idx];
         size_t v = (size_t)q.tile * (HT + 1) + i;
@@ -353,70 +420,148 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
             }
             bprev = ws_bucket((float)KO::from_key(sorted[ls.kpos + pa]), R.lo, R.scale, nb);
         }
+        const uint32_t k32 = (uint32_t)(k >> (KO::BITS - 32));
         int64_t from = bprev + 1, to = bcur;   // inclusive range of buckets
         int64_t cnt = to - from + 1;
+        const DirEntry de{(int32_t)r, k32};
         if (cnt > GAP_INLINE) {
             uint32_t g = atomicAdd(ngaps, 1u);
-            if ((int64_t)g < gap_cap) { gaps[g].pos = ls.dir_pos + from; gaps[g].count = (int32_t)cnt; gaps[g].value = (int32_t)r; }
-            else ws_flag(status, WS_STATUS_INTERNAL);
+            if ((int64_t)g < gap_cap) {
+                gaps[g].pos = ls.dir_pos + from; gaps[g].count = (int32_t)cnt; gaps[g].value = (int32_t)r;
+                gaps[g].key32 = k32;
+            } else ws_flag(status, WS_STATUS_INTERNAL);
         } else {
-            for (int64_t bb = from; bb <= to; ++bb) D[bb] = (int32_t)r;
+            for (int64_t bb = from; bb <= to; ++bb) D[bb] = de;
         }
         if (r == R.n_clusters - 1) {   // tail: buckets after the last start, plus the sentinel
             int64_t f2 = bcur + 1, c2 = (int64_t)nb - bcur;   // buckets bcur+1 .. nb (nb = sentinel)
+            const DirEntry te{(int32_t)R.n_clusters, 0xffffffffu};
             if (c2 > GAP_INLINE) {
                 uint32_t g = atomicAdd(ngaps, 1u);
-                if ((int64_t)g < gap_cap) { gaps[g].pos = ls.dir_pos + f2; gaps[g].count = (int32_t)c2; gaps[g].value = (int32_t)R.n_clusters; }
-                else ws_flag(status, WS_STATUS_INTERNAL);
+                if ((int64_t)g < gap_cap) {
+                    gaps[g].pos = ls.dir_pos + f2; gaps[g].count = (int32_t)c2; gaps[g].value = (int32_t)R.n_clusters;
+                    gaps[g].key32 = 0xffffffffu;
+                } else ws_flag(status, WS_STATUS_INTERNAL);
             } else {
-                for (int64_t bb = f2; bb <= nb; ++bb) D[bb] = (int32_t)R.n_clusters;
+                for (int64_t bb = f2; bb <= nb; ++bb) D[bb] = te;
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(256) k_big_gaps(const BigGap* gaps, const uint32_t* ngaps, int32_t* dir,
+__global__ void __launch_bounds__(256) k_big_gaps(const BigGap* gaps, const uint32_t* ngaps, DirEntry* dir,
                                                   int64_t gap_cap) {
     const int64_t n = min((int64_t)*ngaps, gap_cap);
     for (int64_t g = blockIdx.x; g < n; g += gridDim.x) {
         const BigGap G = gaps[g];
-        for (int i = threadIdx.x; i < G.count; i += 256) dir[G.pos + i] = G.value;
+        const DirEntry e{G.value, G.key32};
+        for (int i = threadIdx.x; i < G.count; i += 256) dir[G.pos + i] = e;
     }
 }
 
 // ---------------------------------------------------------------------------
 // 6. lookup: every weight, in the caller's order, finds its cluster by value
 // ---------------------------------------------------------------------------
+// Last cluster in [lo, hi) whose start key is <= k, else lo - 1; starts from
+// the guess g (interpolated on the 32-bit key prefix) and steps, bisecting if
+// the guess is far off.
+template <typename T>
+__device__ __forceinline__ int ws_find_cluster(const CEntry<T>* tab, int lo, int hi, int g, typename KeyOf<T>::K k,
+                                               typename KeyOf<T>::K kg) {
+    int steps = 0;
+    if (kg <= k) {
+        while (g + 1 < hi && tab[g + 1].key <= k && ++steps < 8) ++g;
+    } else {
+        while (g > lo && tab[g].key > k && ++steps < 8) --g;
+        if (tab[g].key > k) g = lo - 1;
+    }
+    if (steps >= 8) {
+        int l = lo, h = hi;
+        while (l < h) {
+            const int mid = (l + h) >> 1;
+            if (tab[mid].key <= k) l = mid + 1; else h = mid;
+        }
+        g = l - 1;
+    }
+    return g;
+}
+
+// Every weight, in the caller's order, finds its cluster by value: bucket ->
+// directory (L2-resident) -> interpolated probe of the cluster table.  Each
+// thread carries LK elements through every stage so that their independent
+// random loads overlap.
 template <typename T>
 __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, const TileDesc* __restrict__ tiles,
                                                 const LargeSeg* __restrict__ lsegs, const SegRuntime* __restrict__ rt,
-                                                const CEntry<T>* __restrict__ table, const int32_t* __restrict__ dir,
+                                                const CEntry<T>* __restrict__ table, const DirEntry* __restrict__ dir,
                                                 T* out, int32_t* ids, uint32_t* status) {
     typedef KeyOf<T> KO;
+    typedef typename KO::K K;
+    constexpr int LK = 4;
     const TileDesc td = tiles[blockIdx.x];
     const LargeSeg ls = lsegs[td.lseg];
     const SegRuntime R = rt[td.lseg];
     const int nb = 1 << R.dir_log2;
-    const int32_t* D = dir + ls.dir_pos;
+    const DirEntry* D = dir + ls.dir_pos;
     const CEntry<T>* tab = table + R.table_pos;
-    for (int i = threadIdx.x; i < td.len; i += 256) {
-        const T x = values[td.vpos + i];
-        const typename KO::K k = KO::to_key(x);
-        const int b = ws_bucket((float)x, R.lo, R.scale, nb);
-        const int c = (int)R.n_clusters;
-        int lo = D[b], hi = D[b + 1];   // clusters starting in bucket b
-        lo = min(max(lo, 0), c);
-        hi = min(max(hi, lo), c);
-        // last cluster in [lo, hi) whose start key <= k, else lo - 1
-        int l = lo, h = hi;
-        while (l < h) {
-            int mid = (l + h) >> 1;
-            if (tab[mid].key <= k) l = mid + 1; else h = mid;
+    const int c = (int)R.n_clusters;
+    for (int i0 = threadIdx.x; i0 < td.len; i0 += 256 * LK) {
+        T x[LK];
+        K k[LK];
+        int lo[LK], hi[LK], g[LK];
+        DirEntry e0[LK], e1[LK];
+        bool in[LK];
+#pragma unroll
+        for (int u = 0; u < LK; ++u) {
+            const int i = i0 + u * 256;
+            in[u] = i < td.len;
+            x[u] = in[u] ? values[td.vpos + i] : (T)0;
         }
-        int r = l - 1;
-        if (r < 0 || r >= R.n_clusters) { ws_flag(status, WS_STATUS_INTERNAL); r = 0; }
-        out[td.vpos + i] = tab[r].val;
-        if (ids) ids[td.vpos + i] = r;
+#pragma unroll
+        for (int u = 0; u < LK; ++u) {
+            k[u] = KO::to_key(x[u]);
+            const int b = ws_bucket((float)x[u], R.lo, R.scale, nb);
+            e0[u] = D[b];
+            e1[u] = D[b + 1];
+        }
+#pragma unroll
+        for (int u = 0; u < LK; ++u) {
+            const uint32_t k32 = (uint32_t)(k[u] >> (KO::BITS - 32));
+            lo[u] = min(max(e0[u].idx, 0), c);
+            hi[u] = min(max(e1[u].idx, lo[u]), c);
+            if (lo[u] == hi[u] || k32 < e0[u].key32) {
+                g[u] = -1;   // precedes every start in the bucket: cluster lo - 1
+            } else {
+                const uint32_t span = e1[u].key32 - e0[u].key32;
+                int gg = lo[u];
+                if (span > 0) {
+                    const float f = (float)(k32 - e0[u].key32) / (float)span;
+                    gg = lo[u] + (int)(f * (float)(hi[u] - lo[u]));
+                    gg = min(max(gg, lo[u]), hi[u] - 1);
+                }
+                g[u] = gg;
+            }
+        }
+        CEntry<T> cg[LK];
+#pragma unroll
+        for (int u = 0; u < LK; ++u) cg[u] = tab[g[u] >= 0 ? g[u] : max(lo[u] - 1, 0)];
+#pragma unroll
+        for (int u = 0; u < LK; ++u) {
+            int r;
+            CEntry<T> ce = cg[u];
+            if (g[u] < 0) {
+                r = lo[u] - 1;
+            } else {
+                r = ws_find_cluster<T>(tab, lo[u], hi[u], g[u], k[u], ce.key);
+                if (r != g[u] && r >= 0) ce = tab[r];
+            }
+            if (r < 0 || r >= c) { ws_flag(status, WS_STATUS_INTERNAL); r = 0; ce = tab[0]; }
+            if (in[u]) {
+                const int i = i0 + u * 256;
+                out[td.vpos + i] = ce.val;
+                if (ids) ids[td.vpos + i] = r;
+            }
+        }
     }
 }
 

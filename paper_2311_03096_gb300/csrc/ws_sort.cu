@@ -112,12 +112,17 @@ __global__ void __launch_bounds__(WS_SORT_NT, 4) k_onesweep(const T* __restrict_
         const int base = w * 32 * ITEMS + lane;
         if (t < 256) ecount[t] = 0;
         __syncthreads();
+        // issue every load before the first shared-memory atomic so their
+        // latencies overlap
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k) {
             const int p = base + k * 32;
             valid[k] = p < td.len;
             if (FIRST) key[k] = valid[k] ? KO::to_key(values[td.vpos + p]) : (K)0;
             else key[k] = valid[k] ? keys_in[td.kpos + p] : (K)0;
+        }
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
             dg[k] = (uint32_t)((key[k] >> shift) & 0xff);
             if (valid[k]) atomicAdd(&ecount[dg[k]], 1u);
         }
