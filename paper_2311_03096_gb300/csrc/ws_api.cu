@@ -50,9 +50,7 @@ struct ws_plan {
     LargeSeg* d_lsegs = nullptr;
     TileDesc* d_sort_tiles = nullptr;
     TileDesc* d_hull_tiles = nullptr;
-    std::vector<MergeNode*> d_levels;
-    std::vector<int> level_counts;
-    MergeNode* d_nodes_all = nullptr;
+    int n_levels = 0;
     std::vector<void*> allocs;
     void* keys_a = nullptr;
     void* keys_b = nullptr;
@@ -64,7 +62,7 @@ struct ws_plan {
     i128* vx = nullptr;
     int32_t* nvert = nullptr;
     i128* tile_total = nullptr;
-    i128* tile_offset = nullptr;
+    int32_t* arrive = nullptr;
     Piece* pieces = nullptr;
     int32_t* npieces = nullptr;
     int32_t* tile_piece = nullptr;
@@ -98,7 +96,7 @@ LargeWork<T> make_work(const ws_plan* p) {
     W.vx = p->vx;
     W.nvert = p->nvert;
     W.tile_total = p->tile_total;
-    W.tile_offset = p->tile_offset;
+    W.arrive = p->arrive;
     W.pieces = p->pieces;
     W.npieces = p->npieces;
     W.tile_piece = p->tile_piece;
@@ -182,27 +180,9 @@ ws_status build_plan(ws_plan* p) {
     p->n_sort_tiles = (int)stiles.size();
     p->n_hull_tiles = (int)htiles.size();
     p->n_keys = kpos;
-    // merge tree levels (host-built node lists)
-    std::vector<std::vector<MergeNode>> levels;
-    for (int L = 1;; ++L) {
-        std::vector<MergeNode> nodes;
-        bool any = false;
-        for (int i = 0; i < p->n_lseg; ++i) {
-            const LargeSeg& ls = lsegs[i];
-            if (((int64_t)1 << (L - 1)) >= ls.hull_count) continue;
-            any = true;
-            for (int64_t j = 0; (j << L) < ls.hull_count; ++j) {
-                int64_t left = ls.hull_first + (j << L);
-                int64_t right = left + ((int64_t)1 << (L - 1));
-                if (right >= ls.hull_first + ls.hull_count) continue;
-                MergeNode nd;
-                nd.lseg = i; nd.left = (int32_t)left; nd.right = (int32_t)right; nd.pad = 0;
-                nodes.push_back(nd);
-            }
-        }
-        if (!any) break;
-        levels.push_back(nodes);
-    }
+    // merge-tree depth: levels above the tiles of the longest segment
+    p->n_levels = 0;
+    for (const LargeSeg& ls : lsegs) p->n_levels = std::max(p->n_levels, ceil_log2(ls.hull_count) + 1);
     ws_status st;
     std::vector<int64_t> offs(p->h_offsets);
     if ((st = plan_upload(p, &p->d_offsets, offs))) return st;
@@ -212,11 +192,6 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_upload(p, &p->d_lsegs, lsegs))) return st;
     if ((st = plan_upload(p, &p->d_sort_tiles, stiles))) return st;
     if ((st = plan_upload(p, &p->d_hull_tiles, htiles))) return st;
-    std::vector<MergeNode> all;
-    for (auto& lv : levels) { p->level_counts.push_back((int)lv.size()); all.insert(all.end(), lv.begin(), lv.end()); }
-    if ((st = plan_upload(p, &p->d_nodes_all, all))) return st;
-    size_t o = 0;
-    for (auto& lv : levels) { p->d_levels.push_back(p->d_nodes_all + o); o += lv.size(); }
     const int P = f64 ? 8 : 4;
     const size_t nk = (size_t)p->n_keys, nh = (size_t)p->n_hull_tiles, slots = nk + (size_t)p->n_lseg;
     if ((st = plan_alloc(p, &p->keys_a, ksize * nk))) return st;
@@ -232,7 +207,7 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->vx, sizeof(i128) * nh * (WS_HULL_TILE + 1)))) return st;
     if ((st = plan_alloc(p, (void**)&p->nvert, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->tile_total, sizeof(i128) * nh))) return st;
-    if ((st = plan_alloc(p, (void**)&p->tile_offset, sizeof(i128) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->arrive, sizeof(int32_t) * (size_t)p->n_levels * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->pieces, sizeof(Piece) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->npieces, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->tile_piece, sizeof(int32_t) * nh))) return st;
@@ -263,8 +238,7 @@ ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, voi
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);
         e = ws_large_prox<T>(W, (const T*)values, lambdas, (T*)out, ids, n_clusters, fp64, p->ctx->status,
-                             p->ctx->spin_limit, p->d_levels.data(), p->level_counts.data(),
-                             (int)p->level_counts.size(), st);
+                             p->ctx->spin_limit, p->n_levels, st);
         if (e) return map_cuda(e);
     }
     return WS_OK;

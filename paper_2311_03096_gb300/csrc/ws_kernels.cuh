@@ -42,6 +42,7 @@ constexpr int WS_SORT_TILE = WS_SORT_NT * WS_SORT_ITEMS;   // 4096 keys per sort
 constexpr int WS_HULL_NT = 256;              // threads per hull-tile CTA
 constexpr int WS_HULL_M = 16;                // points per thread chunk
 constexpr int WS_HULL_TILE = WS_HULL_NT * WS_HULL_M;       // 4096 elements per hull tile
+constexpr int WS_MAX_LEVELS = 32;           // merge-tree levels (segments < 2^31 elements)
 
 // One tile of a large segment (sort tiles and hull tiles use the same record).
 struct TileDesc {
@@ -66,21 +67,15 @@ struct LargeSeg {
     int32_t pad;
 };
 
-// Merge-tree node (hull-tile level): children are hull-tile ranges.
-struct MergeNode {
-    int32_t lseg;
-    int32_t left;      // global hull-tile index of the left child's first tile
-    int32_t right;     // global hull-tile index of the right child's first tile
-    int32_t pad;
-};
-
 // A piece of a node hull: vertices [lo, hi) of hull tile `tile`; cum = rank of
-// its first vertex within the node hull.
-struct Piece {
+// its first vertex within the node hull; off = fixed-point prefix X at the
+// tile's first point, relative to the node's first point.
+struct __align__(16) Piece {
     int32_t tile;
     uint16_t lo, hi;
     int32_t cum;
     int32_t pad;
+    i128 off;
 };
 
 // Cluster table entry (sorted by key within a segment).
@@ -132,8 +127,8 @@ struct LargeWork {
     uint16_t* vp;            // [n_hull_tiles][WS_HULL_TILE + 1] vertex points (tile-local)
     i128* vx;                // [n_hull_tiles][WS_HULL_TILE + 1] X at vertices (tile-local)
     int32_t* nvert;          // [n_hull_tiles]
-    i128* tile_total;        // [n_hull_tiles]
-    i128* tile_offset;       // [n_hull_tiles] exclusive prefix inside the segment
+    i128* tile_total;        // [n_hull_tiles] node total X, stored at the node's first tile
+    int32_t* arrive;         // [WS_MAX_LEVELS][n_hull_tiles] merge-tree arrival counters
     Piece* pieces;           // [n_hull_tiles]
     int32_t* npieces;        // [n_hull_tiles] pieces of the node whose first tile is this index
     int32_t* tile_piece;     // [n_hull_tiles] piece index in the root list or -1
@@ -151,8 +146,7 @@ cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* stat
                           cudaStream_t st, typename KeyOf<T>::K** sorted);
 template <typename T>
 cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* lambdas, T* out, int32_t* ids,
-                          int64_t* n_clusters, int fp64, uint32_t* status, uint64_t spin_limit,
-                          const MergeNode* const* level_nodes, const int* level_counts, int n_levels,
+                          int64_t* n_clusters, int fp64, uint32_t* status, uint64_t spin_limit, int n_levels,
                           cudaStream_t st);
 template <typename T>
 cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* ids, T* gin, uint32_t* status,

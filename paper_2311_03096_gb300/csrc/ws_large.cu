@@ -19,11 +19,311 @@ constexpr int HNT = WS_HULL_NT;
 constexpr int HM = WS_HULL_M;
 
 // ---------------------------------------------------------------------------
+// 2. merging two adjacent node hulls (run by the CTA that arrives last)
+//
+// Piece lists are rewritten in place as the tree climbs, by whichever CTA
+// merges a node, so they are read through L2 (ld.global.cg): an SM's L1 may
+// still hold a line of a list another SM has since rewritten.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Piece ws_ld_piece(const Piece* p) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    uint4 a = __ldcg(q), b = __ldcg(q + 1);
+    Piece r;
+    *reinterpret_cast<uint4*>(&r) = a;
+    *(reinterpret_cast<uint4*>(&r) + 1) = b;
+    return r;
+}
+__device__ __forceinline__ void ws_st_piece(Piece* p, const Piece& v) {
+    uint4* q = reinterpret_cast<uint4*>(p);
+    __stcg(q, *reinterpret_cast<const uint4*>(&v));
+    __stcg(q + 1, *(reinterpret_cast<const uint4*>(&v) + 1));
+}
+__device__ __forceinline__ i128 ws_ld_i128(const i128* p) {
+    const uint4 v = __ldcg(reinterpret_cast<const uint4*>(p));
+    return *reinterpret_cast<const i128*>(&v);
+}
+
+struct NodeView {
+    const Piece* pc;   // piece list
+    int np;            // pieces
+    const uint16_t* vp;
+    const i128* vx;
+    int hull_first;    // global index of the segment's first hull tile
+    i128 base;         // X offset of this node's first point in the merge frame
+    __device__ __forceinline__ int find(int r) const {   // piece holding rank r
+        int lo = 0, hi = np - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (ws_ld_piece(pc + mid).cum <= r) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ void get(int r, int64_t& pt, i128& X) const {
+        const Piece p = ws_ld_piece(pc + find(r));
+        size_t v = (size_t)p.tile * (HT + 1) + p.lo + (r - p.cum);
+        pt = (int64_t)(p.tile - hull_first) * HT + vp[v];
+        X = base + p.off + vx[v];
+    }
+    __device__ __forceinline__ int count() const {
+        if (np == 0) return 0;
+        const Piece p = ws_ld_piece(pc + np - 1);
+        return p.cum + (p.hi - p.lo);
+    }
+};
+
+__device__ __forceinline__ void ws_piece_vertex(const Piece& q, int v, const uint16_t* vp, const i128* vx,
+                                                int hull_first, i128 base, int64_t& pt, i128& X) {
+    const size_t idx = (size_t)q.tile * (HT + 1) + v;
+    pt = (int64_t)(q.tile - hull_first) * HT + vp[idx];
+    X = base + q.off + vx[idx];
+}
+
+// Bridge between two node hulls by walking outward from their junction
+// (the linear merge of two convex chains), stepping through the piece lists
+// directly.  Returns false (no result) after too many steps; the caller then
+// runs the galloping search.  Same outputs as ws_bridge.
+__device__ bool ws_bridge_walk(const Piece* PL, int npL, const Piece* PR, int npR, const uint16_t* vp,
+                               const i128* vx, int hull_first, i128 baseR, const SegConst& sc, int& flag, int& istar,
+                               int& jstar) {
+    int lp = npL - 1, rp = 0;
+    Piece qL = ws_ld_piece(PL + lp), qR = ws_ld_piece(PR + rp);
+    int lv = qL.hi - 1, rv = qR.lo;   // L_p and R_0: the junction
+    auto prevL = [&](int& p, Piece& q, int& v) -> bool {
+        if (v > q.lo) { --v; return true; }
+        if (p == 0) return false;
+        --p; q = ws_ld_piece(PL + p); v = q.hi - 1; return true;
+    };
+    auto nextR = [&](int& p, Piece& q, int& v) -> bool {
+        if (v + 1 < q.hi) { ++v; return true; }
+        if (p + 1 >= npR) return false;
+        ++p; q = ws_ld_piece(PR + p); v = q.lo; return true;
+    };
+    int64_t pj; i128 Xj;
+    ws_piece_vertex(qR, rv, vp, vx, hull_first, baseR, pj, Xj);
+    if (!prevL(lp, qL, lv) || !nextR(rp, qR, rv)) { flag = 0; return true; }
+    int64_t pl, pr; i128 Xl, Xr;
+    ws_piece_vertex(qL, lv, vp, vx, hull_first, 0, pl, Xl);
+    ws_piece_vertex(qR, rv, vp, vx, hull_first, baseR, pr, Xr);
+    if (ws_convex(Xl, Xj, Xr, pl, pj, pr, sc)) { flag = 0; return true; }
+    flag = 1;
+    int steps = 0;
+    constexpr int WALK_MAX = 32;
+    while (true) {
+        bool moved = false;
+        while (true) {
+            int p2 = lp, v2 = lv;
+            Piece q2 = qL;
+            if (!prevL(p2, q2, v2)) break;
+            int64_t pm; i128 Xm;
+            ws_piece_vertex(q2, v2, vp, vx, hull_first, 0, pm, Xm);
+            if (ws_convex(Xm, Xl, Xr, pm, pl, pr, sc)) break;
+            lp = p2; qL = q2; lv = v2; pl = pm; Xl = Xm; moved = true;
+            if (++steps > WALK_MAX) return false;
+        }
+        while (true) {
+            int p2 = rp, v2 = rv;
+            Piece q2 = qR;
+            if (!nextR(p2, q2, v2)) break;
+            int64_t pn; i128 Xn;
+            ws_piece_vertex(q2, v2, vp, vx, hull_first, baseR, pn, Xn);
+            if (ws_convex(Xl, Xr, Xn, pl, pr, pn, sc)) break;
+            rp = p2; qR = q2; rv = v2; pr = pn; Xr = Xn; moved = true;
+            if (++steps > WALK_MAX) return false;
+        }
+        if (!moved) break;
+    }
+    istar = qL.cum + (lv - qL.lo);
+    jstar = qR.cum + (rv - qR.lo);
+    return true;
+}
+
+constexpr int MW = 16;   // vertices of each child prefetched around the junction
+
+struct MergeSmem {
+    int is, js, pl, pr, npL, npR;
+    i128 totL, totR;
+    int wsi[8];
+    // window: the last MW vertices of L (index 0 = L_p, the junction, going
+    // left) and the first MW of R (index 0 = R_0 = junction, going right)
+    Piece wpL[MW], wpR[MW];        // the pieces at the ends of the two lists
+    int nwpL, nwpR;
+    int wLn, wRn;                  // vertices in each window
+    int wLpc[MW], wLv[MW], wRpc[MW], wRv[MW];   // (piece slot in the list, vertex index)
+    int64_t wLpt[MW], wRpt[MW];
+    i128 wLX[MW], wRX[MW];
+    int ok;
+};
+
+// Merge the node hulls whose piece lists start at Lg and Rg (global hull-tile
+// indices, Rg > Lg adjacent); the result replaces the list at Lg.  All
+// threads of the CTA call this.  Warp 0 first gathers, in parallel, the
+// vertices next to the junction (usually all the bridge needs); thread 0
+// walks them in shared memory and falls back to the global search only if
+// the bridge leaves that window.
+__device__ __noinline__ void ws_merge_children(MergeSmem& m, Piece* pieces, int32_t* npieces, i128* ntotal, int Lg, int Rg,
+                                  const uint16_t* vp, const i128* vx, int hull_first, const SegConst& sc) {
+    const int t = threadIdx.x;
+    Piece* PL = pieces + Lg;
+    Piece* PR = pieces + Rg;
+    if (t < 32) {
+        const int npL = __ldcg(npieces + Lg), npR = __ldcg(npieces + Rg);
+        // the last MW pieces of L (slot 0 = last) and the first MW of R
+        if (t < MW) { if (t < npL) m.wpL[t] = ws_ld_piece(PL + npL - 1 - t); }
+        else { const int k = t - MW; if (k < npR) m.wpR[k] = ws_ld_piece(PR + k); }
+        if (t == 0) {
+            m.npL = npL; m.npR = npR;
+            m.totL = ws_ld_i128(ntotal + Lg);
+            m.totR = ws_ld_i128(ntotal + Rg);
+            m.nwpL = min(npL, MW); m.nwpR = min(npR, MW);
+        }
+        __syncwarp();
+        if (t == 0) {   // enumerate the window's vertices
+            int n = 0;
+            for (int k = 0; k < m.nwpL && n < MW; ++k) {
+                const Piece q = m.wpL[k];
+                for (int v = q.hi - 1; v >= (int)q.lo && n < MW; --v) { m.wLpc[n] = npL - 1 - k; m.wLv[n] = v; ++n; }
+            }
+            m.wLn = n;
+            n = 0;
+            for (int k = 0; k < m.nwpR && n < MW; ++k) {
+                const Piece q = m.wpR[k];
+                for (int v = q.lo; v < (int)q.hi && n < MW; ++v) { m.wRpc[n] = k; m.wRv[n] = v; ++n; }
+            }
+            m.wRn = n;
+        }
+        __syncwarp();
+        if (t < MW) {
+            if (t < m.wLn) {
+                const Piece q = m.wpL[npL - 1 - m.wLpc[t]];
+                ws_piece_vertex(q, m.wLv[t], vp, vx, hull_first, 0, m.wLpt[t], m.wLX[t]);
+            }
+        } else {
+            const int k = t - MW;
+            if (k < m.wRn) {
+                const Piece q = m.wpR[m.wRpc[k]];
+                ws_piece_vertex(q, m.wRv[k], vp, vx, hull_first, m.totL, m.wRpt[k], m.wRX[k]);
+            }
+        }
+        __syncwarp();
+        if (t == 0) {
+            // walk in the window: li indexes wL (0 = junction), rj indexes wR (0 = junction)
+            const int nL = m.wLn, nR = m.wRn;
+            int flag = 0, li = 0, rj = 0;
+            bool ok = true;
+            const bool Lmore = nL == MW, Rmore = nR == MW;   // a list may continue past the window
+            if (nL >= 2 && nR >= 2) {
+                if (!ws_convex(m.wLX[1], m.wLX[0], m.wRX[1], m.wLpt[1], m.wLpt[0], m.wRpt[1], sc)) {
+                    flag = 1; li = 1; rj = 1;
+                    while (ok) {
+                        bool moved = false;
+                        while (true) {
+                            if (li + 1 >= nL) { if (Lmore) ok = false; break; }
+                            if (ws_convex(m.wLX[li + 1], m.wLX[li], m.wRX[rj], m.wLpt[li + 1], m.wLpt[li], m.wRpt[rj], sc))
+                                break;
+                            ++li; moved = true;
+                        }
+                        if (!ok) break;
+                        while (true) {
+                            if (rj + 1 >= nR) { if (Rmore) ok = false; break; }
+                            if (ws_convex(m.wLX[li], m.wRX[rj], m.wRX[rj + 1], m.wLpt[li], m.wRpt[rj], m.wRpt[rj + 1], sc))
+                                break;
+                            ++rj; moved = true;
+                        }
+                        if (!moved) break;
+                    }
+                }
+            } else if (!(nL == 1 || nR == 1)) {
+                ok = false;
+            }
+            if (ok) {
+                if (flag == 0) {   // junction stays: keep all of L, drop R_0
+                    m.pl = npL - 1;
+                    const Piece qL = ws_ld_piece(PL + m.pl);
+                    m.is = qL.cum + (qL.hi - qL.lo) - 1;
+                    m.js = 1;
+                    if (nR >= 2) { m.pr = m.wRpc[1]; } else { m.pr = npR; }
+                } else {
+                    m.pl = m.wLpc[li];
+                    m.pr = m.wRpc[rj];
+                    const Piece qL = ws_ld_piece(PL + m.pl);
+                    const Piece qR = ws_ld_piece(PR + m.pr);
+                    m.is = qL.cum + (m.wLv[li] - qL.lo);
+                    m.js = qR.cum + (m.wRv[rj] - qR.lo);
+                }
+                if (nL == 1 || nR == 1) { m.pl = npL - 1; m.is = -1; m.pr = (nR >= 2) ? m.wRpc[1] : npR; m.js = 1; }
+            }
+            m.ok = ok ? 1 : 0;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (t == 0) {
+        const int npL = m.npL, npR = m.npR;
+        const i128 totL = m.totL;
+        if (!m.ok) {   // the bridge reaches beyond the window: global walk, then the gallop
+            NodeView L{PL, npL, vp, vx, hull_first, 0};
+            NodeView R{PR, npR, vp, vx, hull_first, totL};
+            const int nL = L.count(), nR = R.count();
+            int flag = 0, is = nL - 1, js = 0;
+            if (nL > 0 && nR > 0) {
+                if (!ws_bridge_walk(PL, npL, PR, npR, vp, vx, hull_first, totL, sc, flag, is, js)) {
+                    auto gl = [&](int r, int64_t& pt, i128& X) { L.get(r, pt, X); };
+                    auto gr = [&](int r, int64_t& pt, i128& X) { R.get(r, pt, X); };
+                    ws_bridge(gl, nL - 1, gr, nR - 1, sc, flag, is, js);
+                }
+                if (flag == 0) { is = nL - 1; js = 1; }
+            }
+            m.pl = (nL > 0) ? L.find(is) : -1;
+            m.pr = (nR > 0 && js < nR) ? R.find(js) : npR;
+            m.is = is; m.js = js;
+        }
+        if (m.pl >= 0 && m.is >= 0) {   // truncate the left list after istar
+            Piece q = ws_ld_piece(PL + m.pl);
+            q.hi = (uint16_t)(q.lo + (m.is - q.cum) + 1);
+            ws_st_piece(PL + m.pl, q);
+        }
+        if (m.pr < npR) {  // the right list starts at jstar
+            Piece q = ws_ld_piece(PR + m.pr);
+            q.lo = (uint16_t)(q.lo + (m.js - q.cum));
+            ws_st_piece(PR + m.pr, q);
+        }
+    }
+    __syncthreads();
+    const int keepL = m.pl + 1, firstR = m.pr, keepR = m.npR - m.pr;
+    const i128 totL = m.totL;
+    // Move the right suffix down behind the left prefix (dst <= src: chunked),
+    // rebasing offsets onto the left node's first point.  Ranks of the kept
+    // left pieces are unchanged; the right ones shift uniformly: the first
+    // kept right piece starts at rank istar + 1.
+    const int shift = m.is + 1 - m.js;
+    for (int b = 0; b < keepR; b += 256) {
+        Piece v;
+        const bool has = b + t < keepR;
+        if (has) {
+            v = ws_ld_piece(PR + firstR + b + t);
+            v.off += totL;
+            v.cum = (b + t == 0) ? m.is + 1 : v.cum + shift;
+        }
+        __syncthreads();
+        if (has) ws_st_piece(PL + keepL + b + t, v);
+        __syncthreads();
+    }
+    const int np = keepL + keepR;
+    if (t == 0) {
+        __stcg(npieces + Lg, np);
+        const i128 tot = m.totL + m.totR;
+        __stcg(reinterpret_cast<uint4*>(ntotal + Lg), *reinterpret_cast<const uint4*>(&tot));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // 1. per-tile hull
 // ---------------------------------------------------------------------------
 struct TileHullSmem {
     TilePrefix<HNT, HM> pre;
     HullSmem<HNT, HM> hull;
+    MergeSmem ms;
+    int go;
     SegConst sc;     // global fixed-point scale of the segment
     SegConst sct;    // scale of this tile when it lies in one binade
     float muq, muqt;
@@ -31,12 +331,13 @@ struct TileHullSmem {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(HNT) k_tile_hull(const typename KeyOf<T>::K* __restrict__ sorted,
+__global__ void __launch_bounds__(HNT, 3) k_tile_hull(const typename KeyOf<T>::K* __restrict__ sorted,
                                                    const TileDesc* __restrict__ htiles,
                                                    const LargeSeg* __restrict__ lsegs,
                                                    const double* __restrict__ lambdas, SegRuntime* rt,
                                                    uint16_t* vp, i128* vx, int32_t* nvert, i128* tile_total,
-                                                   Piece* pieces, int32_t* npieces, uint32_t* status) {
+                                                   Piece* pieces, int32_t* npieces, int32_t* arrive, int n_hull,
+                                                   uint32_t* status) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -110,207 +411,32 @@ __global__ void __launch_bounds__(HNT) k_tile_hull(const typename KeyOf<T>::K* _
     }
     if (t == 0) {
         nvert[tile] = nv;
-        tile_total[tile] = total;
+        __stcg(reinterpret_cast<uint4*>(tile_total + tile), *reinterpret_cast<const uint4*>(&total));
         Piece pc;
-        pc.tile = tile; pc.lo = 0; pc.hi = (uint16_t)nv; pc.cum = 0; pc.pad = 0;
-        pieces[tile] = pc;
-        npieces[tile] = 1;
+        pc.tile = tile; pc.lo = 0; pc.hi = (uint16_t)nv; pc.cum = 0; pc.pad = 0; pc.off = 0;
+        ws_st_piece(pieces + tile, pc);
+        __stcg(npieces + tile, 1);
     }
-}
-
-// ---------------------------------------------------------------------------
-// 2. exclusive scan of tile totals inside each segment
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_tile_scan(const LargeSeg* __restrict__ lsegs, const i128* tile_total,
-                                                   i128* tile_offset) {
-    __shared__ i128 ws[8];
-    const LargeSeg ls = lsegs[blockIdx.x];
-    i128 carry = 0;
-    for (int b = 0; b < ls.hull_count; b += 256) {
-        int i = b + threadIdx.x;
-        i128 v = (i < ls.hull_count) ? tile_total[ls.hull_first + i] : (i128)0;
-        i128 tot;
-        i128 ex = ws_block_excl_scan<256, i128>(v, ws, &tot);
-        if (i < ls.hull_count) tile_offset[ls.hull_first + i] = carry + ex;
-        carry += tot;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// 3. merge of two adjacent node hulls (one CTA per node)
-// ---------------------------------------------------------------------------
-struct NodeView {
-    const Piece* pc;   // piece list
-    int np;            // pieces
-    const uint16_t* vp;
-    const i128* vx;
-    const i128* toff;
-    int hull_first;    // global index of the segment's first hull tile
-    __device__ __forceinline__ int find(int r) const {   // piece holding rank r
-        int lo = 0, hi = np - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (pc[mid].cum <= r) lo = mid; else hi = mid - 1;
-        }
-        return lo;
-    }
-    __device__ __forceinline__ void get(int r, int64_t& pt, i128& X) const {
-        const Piece p = pc[find(r)];
-        size_t v = (size_t)p.tile * (HT + 1) + p.lo + (r - p.cum);
-        pt = (int64_t)(p.tile - hull_first) * HT + vp[v];
-        X = toff[p.tile] + vx[v];
-    }
-    __device__ __forceinline__ int count() const {
-        if (np == 0) return 0;
-        const Piece p = pc[np - 1];
-        return p.cum + (p.hi - p.lo);
-    }
-};
-
-// Bridge between two node hulls by walking outward from their junction
-// (the linear merge of two convex chains), stepping through the piece lists
-// directly.  Returns false (no result) after too many steps; the caller then
-// runs the galloping search.  Same outputs as ws_bridge.
-__device__ __forceinline__ void ws_piece_vertex(const Piece* P, int pi, int v, const uint16_t* vp, const i128* vx,
-                                                const i128* toff, int hull_first, int64_t& pt, i128& X) {
-    const Piece q = P[pi];
-    const size_t idx = (size_t)q.tile * (HT + 1) + v;
-    pt = (int64_t)(q.tile - hull_first) * HT + vp[idx];
-    X = toff[q.tile] + vx[idx];
-}
-
-__device__ bool ws_bridge_walk(const Piece* PL, int npL, const Piece* PR, int npR, const uint16_t* vp,
-                               const i128* vx, const i128* toff, int hull_first, const SegConst& sc, int& flag,
-                               int& istar, int& jstar) {
-    // cursors: (piece, vertex index in the tile list)
-    int lp = npL - 1, lv = PL[lp].hi - 1;   // L_p = junction
-    int rp = 0, rv = PR[0].lo;              // R_0 = junction
-    auto prevL = [&](int& p, int& v) -> bool {
-        if (v > PL[p].lo) { --v; return true; }
-        if (p == 0) return false;
-        --p; v = PL[p].hi - 1; return true;
-    };
-    auto nextR = [&](int& p, int& v) -> bool {
-        if (v + 1 < PR[p].hi) { ++v; return true; }
-        if (p + 1 >= npR) return false;
-        ++p; v = PR[p].lo; return true;
-    };
-    int64_t pj; i128 Xj;
-    ws_piece_vertex(PR, rp, rv, vp, vx, toff, hull_first, pj, Xj);
-    if (!prevL(lp, lv) || !nextR(rp, rv)) { flag = 0; return true; }   // a one-vertex side: nothing to merge
-    int64_t pl, pr; i128 Xl, Xr;
-    ws_piece_vertex(PL, lp, lv, vp, vx, toff, hull_first, pl, Xl);
-    ws_piece_vertex(PR, rp, rv, vp, vx, toff, hull_first, pr, Xr);
-    if (ws_convex(Xl, Xj, Xr, pl, pj, pr, sc)) { flag = 0; return true; }
-    flag = 1;
-    int steps = 0;
-    constexpr int WALK_MAX = 32;
-    while (true) {
-        bool moved = false;
-        while (true) {
-            int p2 = lp, v2 = lv;
-            if (!prevL(p2, v2)) break;
-            int64_t pm; i128 Xm;
-            ws_piece_vertex(PL, p2, v2, vp, vx, toff, hull_first, pm, Xm);
-            if (ws_convex(Xm, Xl, Xr, pm, pl, pr, sc)) break;
-            lp = p2; lv = v2; pl = pm; Xl = Xm; moved = true;
-            if (++steps > WALK_MAX) return false;
-        }
-        while (true) {
-            int p2 = rp, v2 = rv;
-            if (!nextR(p2, v2)) break;
-            int64_t pn; i128 Xn;
-            ws_piece_vertex(PR, p2, v2, vp, vx, toff, hull_first, pn, Xn);
-            if (ws_convex(Xl, Xr, Xn, pl, pr, pn, sc)) break;
-            rp = p2; rv = v2; pr = pn; Xr = Xn; moved = true;
-            if (++steps > WALK_MAX) return false;
-        }
-        if (!moved) break;
-    }
-    istar = PL[lp].cum + (lv - PL[lp].lo);
-    jstar = PR[rp].cum + (rv - PR[rp].lo);
-    return true;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_merge(const MergeNode* __restrict__ nodes, const LargeSeg* __restrict__ lsegs,
-                                               const double* __restrict__ lambdas, const SegRuntime* __restrict__ rt,
-                                               const uint16_t* __restrict__ vp, const i128* __restrict__ vx,
-                                               const i128* __restrict__ toff, Piece* pieces, int32_t* npieces,
-                                               uint32_t* status) {
-    __shared__ int s_is, s_js, s_flag, s_pl, s_pr;
-    __shared__ int wsi[8];
-    const MergeNode nd = nodes[blockIdx.x];
-    const LargeSeg ls = lsegs[nd.lseg];
-    const int t = threadIdx.x;
-    Piece* PL = pieces + nd.left;
-    Piece* PR = pieces + nd.right;
-    const int npL = npieces[nd.left], npR = npieces[nd.right];
-    if (t == 0) {
-        double lam = lambdas[ls.seg];
-        if (!(lam >= 0.0) || !(lam <= 1.7976931348623157e308)) lam = 0.0;
-        const SegConst sc = ws_seg_const<T>(ls.len, lam, rt[nd.lseg].emax);
-        NodeView L{PL, npL, vp, vx, toff, ls.hull_first};
-        NodeView R{PR, npR, vp, vx, toff, ls.hull_first};
-        int nL = L.count(), nR = R.count();
-        int flag = 0, is = nL - 1, js = 0;
-        if (nL > 0 && nR > 0) {
-            if (!ws_bridge_walk(PL, npL, PR, npR, vp, vx, toff, ls.hull_first, sc, flag, is, js)) {
-                auto gl = [&](int r, int64_t& pt, i128& X) { L.get(r, pt, X); };
-                auto gr = [&](int r, int64_t& pt, i128& X) { R.get(r, pt, X); };
-                ws_bridge(gl, nL - 1, gr, nR - 1, sc, flag, is, js);
-            }
-            if (flag == 0) { is = nL - 1; js = 1; }
-        }
-        // pieces holding istar and jstar
-        s_pl = (nL > 0) ? L.find(is) : -1;
-        s_pr = (nR > 0 && js < nR) ? R.find(js) : npR;
-        s_is = is; s_js = js; s_flag = flag;
-        // truncate the left list at istar
-        if (s_pl >= 0) {
-            Piece p = PL[s_pl];
-            p.hi = (uint16_t)(p.lo + (is - p.cum) + 1);
-            PL[s_pl] = p;
-        }
-        if (s_pr < npR) {
-            Piece p = PR[s_pr];
-            int newlo = p.lo + (js - p.cum);
-            p.lo = (uint16_t)newlo;
-            PR[s_pr] = p;
-        }
-    }
-    __syncthreads();
-    const int keepL = s_pl + 1;                // pieces kept from the left list
-    const int firstR = s_pr;                   // first piece kept from the right list
-    const int keepR = npR - firstR;
-    // move the right suffix down behind the left prefix (dst <= src: chunked copy)
-    Piece* dst = PL + keepL;
-    const Piece* src = PR + firstR;
-    for (int b = 0; b < keepR; b += 256) {
-        Piece v;
-        bool has = b + t < keepR;
-        if (has) v = src[b + t];
+    // Climb the merge tree: at each level the CTA that finishes second merges
+    // the two children of the parent; the first one exits.  Nobody waits.
+    const int nt = ls.hull_count, tin = td.tin;
+    for (int level = 0; (1 << level) < nt; ++level) {
+        const int span = 1 << level;
+        const int parent_base = (tin >> (level + 1)) << (level + 1);
+        const int right_base = parent_base + span;
+        if (right_base >= nt) continue;   // no right sibling: the parent is this node
+        __threadfence();                  // this CTA's writes of the child are visible GPU-wide ...
         __syncthreads();
-        if (has) dst[b + t] = v;
+        if (t == 0) {                     // ... before its arrival is counted
+            const int old = atomicAdd(&arrive[(size_t)(level + 1) * n_hull + ls.hull_first + parent_base], 1);
+            __threadfence();
+            s.go = (old == 1);
+        }
         __syncthreads();
+        if (!s.go) break;
+        ws_merge_children(s.ms, pieces, npieces, tile_total, ls.hull_first + parent_base, ls.hull_first + right_base,
+                          vp, vx, ls.hull_first, s.sc);
     }
-    // recompute the ranks of the merged list (drop empty pieces is not needed:
-    // a kept piece always holds >= 1 vertex)
-    const int np = keepL + keepR;
-    int carry = 0;
-    for (int b = 0; b < np; b += 256) {
-        int i = b + t;
-        int c = 0;
-        Piece v;
-        if (i < np) { v = PL[i]; c = v.hi - v.lo; }
-        int tot;
-        int ex = ws_block_excl_scan<256, int>(c, wsi, &tot);
-        if (i < np) { v.cum = carry + ex; PL[i] = v; }
-        carry += tot;
-        __syncthreads();
-    }
-    if (t == 0) npieces[nd.left] = np;
-    (void)status;
 }
 
 // ---------------------------------------------------------------------------
@@ -366,7 +492,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
                                                const double* __restrict__ lambdas, const SegRuntime* __restrict__ rt,
                                                const typename KeyOf<T>::K* __restrict__ sorted,
                                                const uint16_t* __restrict__ vp, const i128* __restrict__ vx,
-                                               const i128* __restrict__ toff, const Piece* __restrict__ pieces,
+                                               const Piece* __restrict__ pieces,
                                                const int32_t* __restrict__ npieces,
                                                const int32_t* __restrict__ tile_piece, CEntry<T>* table,
                                                DirEntry* dir, BigGap* gaps, uint32_t* ngaps, int64_t gap_cap,
@@ -390,7 +516,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
         const Piece q = P[piece_idx];
         size_t v = (size_t)q.tile * (HT + 1) + i;
         pt = (int64_t)(q.tile - ls.hull_first) * HT + vp[v];
-        X = toff[q.tile] + vx[v];
+        X = q.off + vx[v];
     };
     for (int i = pc.lo + threadIdx.x; i < pc.hi; i += 256) {
         int64_t r = (int64_t)pc.cum + (i - pc.lo);
@@ -612,8 +738,7 @@ __global__ void k_copy_sorted(const typename KeyOf<T>::K* __restrict__ sorted, c
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* lambdas, T* out, int32_t* ids,
-                          int64_t* n_clusters, int fp64, uint32_t* status, uint64_t spin_limit,
-                          const MergeNode* const* level_nodes, const int* level_counts, int n_levels,
+                          int64_t* n_clusters, int fp64, uint32_t* status, uint64_t spin_limit, int n_levels,
                           cudaStream_t st) {
     typedef typename KeyOf<T>::K K;
     if (W.n_lseg == 0) return cudaSuccess;
@@ -623,16 +748,12 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
     size_t smem = sizeof(TileHullSmem);
     e = cudaFuncSetAttribute(k_tile_hull<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
+    e = cudaMemsetAsync(W.arrive, 0, sizeof(int32_t) * (size_t)n_levels * W.n_hull_tiles, st);
+    if (e) return e;
     WS_LAUNCH(W.prof, WSK_TILE_HULL, st,
               (k_tile_hull<T><<<W.n_hull_tiles, HNT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp,
                                                                 W.vx, W.nvert, W.tile_total, W.pieces, W.npieces,
-                                                                status)));
-    WS_LAUNCH(W.prof, WSK_TILE_SCAN, st, (k_tile_scan<<<W.n_lseg, 256, 0, st>>>(W.lsegs, W.tile_total, W.tile_offset)));
-    for (int l = 0; l < n_levels; ++l)
-        if (level_counts[l] > 0)
-            WS_LAUNCH(W.prof, WSK_MERGE, st,
-                      (k_merge<T><<<level_counts[l], 256, 0, st>>>(level_nodes[l], W.lsegs, lambdas, W.rt, W.vp, W.vx,
-                                                                  W.tile_offset, W.pieces, W.npieces, status)));
+                                                                W.arrive, W.n_hull_tiles, status)));
     e = cudaMemsetAsync(W.tile_piece, 0xff, sizeof(int32_t) * (size_t)W.n_hull_tiles, st);
     if (e) return e;
     WS_LAUNCH(W.prof, WSK_ROOT, st,
@@ -646,7 +767,7 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
     if (e) return e;
     WS_LAUNCH(W.prof, WSK_TABLE, st,
               (k_table<T><<<W.n_hull_tiles, 256, 0, st>>>(W.hull_tiles, W.lsegs, lambdas, W.rt, sorted, W.vp, W.vx,
-                                                         W.tile_offset, W.pieces, W.npieces, W.tile_piece, W.table,
+                                                         W.pieces, W.npieces, W.tile_piece, W.table,
                                                          W.dir, gaps, ngaps, gap_cap, fp64, status)));
     WS_LAUNCH(W.prof, WSK_BIG_GAPS, st, (k_big_gaps<<<1024, 256, 0, st>>>(gaps, ngaps, W.dir, gap_cap)));
     WS_LAUNCH(W.prof, WSK_LOOKUP, st,
@@ -681,8 +802,7 @@ cudaError_t ws_large_copy_sorted(const LargeWork<T>& W, const typename KeyOf<T>:
 
 #define WS_INST(T)                                                                                                  \
     template cudaError_t ws_large_prox<T>(const LargeWork<T>&, const T*, const double*, T*, int32_t*, int64_t*, int, \
-                                          uint32_t*, uint64_t, const MergeNode* const*, const int*, int,            \
-                                          cudaStream_t);                                                            \
+                                          uint32_t*, uint64_t, int, cudaStream_t);                                  \
     template cudaError_t ws_large_backward<T>(const LargeWork<T>&, const T*, const int32_t*, T*, uint32_t*,         \
                                               cudaStream_t);                                                        \
     template cudaError_t ws_large_copy_sorted<T>(const LargeWork<T>&, const typename KeyOf<T>::K*, T*, cudaStream_t);
