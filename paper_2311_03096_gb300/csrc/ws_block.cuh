@@ -348,18 +348,56 @@ static __device__ __noinline__ bool ws_convex_binade_exact(int64_t A, int64_t B,
     return (Lv << (128 - bl)) > (Rv << (128 - br));
 }
 
-// Binade tiles: FP32 filter with a rigorous bound (as in TilePts), then the
-// exact integer test for near-ties.
+// Binade tiles.  When range * n^2 <= 2^62 (always for FP32 keys), Delta =
+// B n1 - A n2 is exact in 64 bits and only the right-hand side mu (c-a) n1 n2
+// is rounded, so the FP32 filter's error is relative to |Delta| + rhs rather
+// than to the cancelling terms B n1 and A n2: Delta is converted once (2^-24),
+// mu, the product and the multiply add <= 4 roundings to rhs (2^-24 each) and
+// the subtraction one more, < 3.1e-7 (Delta + rhs) in all; the 6e-7 margin
+// covers that twice.  Otherwise (FP64 keys spread over a wide range) the
+// filter runs on the rounded terms as in TilePts.  Near-ties fall through to
+// the exact integer test.
 template <int M>
 struct TilePtsBinade {
     const int64_t* s64;
-    float muq;   // lambda 2^L_tile / (d - 1)
+    float muq;       // lambda 2^L_tile / (d - 1)
     bool fast;
+    bool d64;        // range * n^2 <= 2^62: Delta is exact in 64 bits
+    uint64_t modd;   // lambda 2^L_tile = modd * 2^sodd with modd odd (0 if lambda = 0)
+    int sodd;
     __device__ __forceinline__ int64_t v(int p) const { return s64[ws_sidx<M>(p)]; }
+    // Exact test Delta (d-1) > modd K 2^sodd for Delta > 0 when both sides fit
+    // in 63 bits (the usual near-tie: lambda 2^L / (d-1) close to a short
+    // dyadic number); 1 = convex, 0 = not, -1 = too wide here.
+    __device__ __forceinline__ int near_tie64(int64_t D, uint64_t K, const SegConst& sc) const {
+        const uint64_t Lh = __umul64hi((uint64_t)D, sc.dm1), Ll = (uint64_t)D * sc.dm1;
+        const uint64_t Rh = __umul64hi(modd, K), Rl = modd * K;
+        if (Lh != 0 || Rh != 0 || (Ll >> 63) != 0 || (Rl >> 63) != 0) return -1;
+        if (sodd >= 0) {
+            if (sodd > 62 || (Rl >> (63 - sodd)) != 0) return -1;
+            return Ll > (Rl << sodd) ? 1 : 0;
+        }
+        if (-sodd > 62 || (Ll >> (63 + sodd)) != 0) return -1;
+        return (Ll << -sodd) > Rl ? 1 : 0;
+    }
     __device__ __forceinline__ bool convex_v(int a, int64_t va, int b, int64_t vb, int c, int64_t vc,
                                              const SegConst& sc) const {
         const int64_t A = vb - va, B = vc - vb;
-        if (fast) {
+        if (d64) {
+            const int64_t D = B * (int64_t)(b - a) - A * (int64_t)(c - b);
+            if (D <= 0) return false;
+            if (modd == 0) return true;
+            if (fast) {
+                const float Df = (float)D;
+                const float rhs = muq * ((float)(c - a) * (float)((b - a) * (c - b)));
+                const float diff = Df - rhs;
+                const float err = 6.0e-7f * (Df + rhs);
+                if (diff > err) return true;
+                if (diff < -err) return false;
+            }
+            const int r = near_tie64(D, (uint64_t)(c - a) * (uint64_t)(b - a) * (uint64_t)(c - b), sc);
+            if (r >= 0) return r != 0;
+        } else if (fast) {
             const float n1 = (float)(b - a), n2 = (float)(c - b);
             const float fB = (float)B * n1;
             const float fA = (float)A * n2;
@@ -375,6 +413,24 @@ struct TilePtsBinade {
         return convex_v(a, v(a), b, v(b), c, v(c), sc);
     }
 };
+
+// True when a binade tile's keys k0..kn (n keys) keep B n1 - A n2 exact in
+// 64 bits: |B n1|, |A n2| <= n1 n2 (kn - k0) <= n^2 (kn - k0) / 4.
+template <typename K>
+__device__ __forceinline__ bool ws_binade_d64(K k0, K kn, int n) {
+    return n <= 1 || (uint64_t)(kn - k0) <= (((uint64_t)1 << 62) / (uint64_t)n) / (uint64_t)n;
+}
+
+// Binade points of a tile with constants sc (fixed-point scale of the tile).
+template <int M, typename K>
+__device__ __forceinline__ TilePtsBinade<M> ws_binade_pts(const int64_t* s64, float muq, bool fast, K k0, K kn,
+                                                          int n, const SegConst& sc) {
+    TilePtsBinade<M> P;
+    P.s64 = s64; P.muq = muq; P.fast = fast; P.d64 = ws_binade_d64<K>(k0, kn, n);
+    if (sc.mlam == 0) { P.modd = 0; P.sodd = 0; }
+    else { const int tz = __ffsll((long long)sc.mlam) - 1; P.modd = sc.mlam >> tz; P.sodd = sc.s + tz; }
+    return P;
+}
 
 // Rank -> point in the hull of chunks [c0, c1) (ranks relative to cum[c0]).
 template <int NT, int M>

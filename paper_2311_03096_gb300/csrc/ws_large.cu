@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(HNT, 3) k_tile_hull(const typename KeyOf<T>::K
     const int mode = ws_tile_prefix<T, HNT, HM>(s.pre, kr, kfirst, klast, n, emax, q0, total, bsh);
     int nv;
     if (mode == WS_TILE_BINADE) {
-        const TilePtsBinade<HM> P{s.pre.s64, s.muqt, s.fastt != 0};
+        const TilePtsBinade<HM> P = ws_binade_pts<HM, K>(s.pre.s64, s.muqt, s.fastt != 0, kfirst, klast, n, s.sct);
         ws_cta_hull<HNT, HM>(s.hull, n, P, s.sct, &nv);
     } else if (mode == WS_TILE_NARROW) {
         const TilePts<HM, true> P{s.pre.s64, s.pre.base, q0, s.muq, s.fast != 0};

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
     // ---- exact hull (in-CTA merge)
     int nv;
     if (mode == WS_TILE_BINADE) {
-        const TilePtsBinade<M> P{s.pre.s64, s.muqt, s.fastt != 0};
+        const TilePtsBinade<M> P = ws_binade_pts<M, K>(s.pre.s64, s.muqt, s.fastt != 0, s.keys[0], s.keys[n - 1], n, s.sct);
         ws_cta_hull<NT, M>(s.hull, n, P, s.sct, &nv);
     } else if (mode == WS_TILE_NARROW) {
         const TilePts<M, true> P{s.pre.s64, s.pre.base, q0, s.muq, s.fast != 0};

@@ -83,17 +83,19 @@ __global__ void __launch_bounds__(WS_SORT_NT, 4) k_onesweep(const T* __restrict_
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     constexpr int P = KO::BITS / 8;
-    constexpr int NT = WS_SORT_NT, ITEMS = WS_SORT_ITEMS, TILE = WS_SORT_TILE;
+    constexpr int NT = WS_SORT_NT, ITEMS = WS_SORT_ITEMS, TILE = WS_SORT_TILE, NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K* skeys = reinterpret_cast<K*>(smem_raw);
-    uint32_t* whist = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * TILE);
-    uint32_t* dcount = whist + (NT / 32) * WS_SORT_CHAINS * 256;
-    uint32_t* dstart = dcount + 256;
+    uint32_t* whist = reinterpret_cast<uint32_t*>(smem_raw + sizeof(K) * TILE);   // [NW][256] per-warp counts
+    uint32_t* mbins = whist + NW * 256;                                             // [NW][256] peer masks
+    uint32_t* dstart = mbins + NW * 256;
     int64_t* gbase = reinterpret_cast<int64_t*>(dstart + 256);
-    __shared__ uint32_t ecount[256];
     __shared__ int s_tile;
     __shared__ int s_timeout;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint32_t* my = whist + w * 256;
+    uint32_t* mb = mbins + w * 256;
+    for (int i = lane; i < 256; i += 32) { my[i] = 0; mb[i] = 0; }
     if (t == 0) { s_tile = (int)atomicAdd(counter, 1u); s_timeout = 0; }
     __syncthreads();
     const int tile = s_tile;
@@ -102,41 +104,72 @@ __global__ void __launch_bounds__(WS_SORT_NT, 4) k_onesweep(const T* __restrict_
     const uint32_t* dbase = hist + ((size_t)td.lseg * P + pass) * 256;
     const uint64_t ep = (uint64_t)(*epoch_p) << LB_EPOCH_SHIFT;
     const int shift = 8 * pass;
+    uint64_t* my_lb = lookback + (size_t)tile * 256;
 
+    // Warp w holds keys [w*32*ITEMS, (w+1)*32*ITEMS) of the tile, item k of
+    // lane l being key w*32*ITEMS + 32k + l, so ranking items in order k and
+    // lanes in order l is stable.
     K key[ITEMS];
     int pos[ITEMS];
-    uint64_t* my_lb = lookback + (size_t)tile * 256;
+    const int base = w * 32 * ITEMS + lane;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        const int p = base + k * 32;
+        const bool v = p < td.len;
+        if (FIRST) key[k] = v ? KO::to_key(values[td.vpos + p]) : (K)0;
+        else key[k] = v ? keys_in[td.kpos + p] : (K)0;
+    }
+    // Rank within the warp: the lanes holding the same digit find each other
+    // by OR-ing their lane bits into the digit's shared-memory word; the
+    // lowest of them advances the warp's count of that digit.
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        const bool v = base + k * 32 < td.len;
+        const uint32_t dg = (uint32_t)(key[k] >> shift) & 0xffu;
+        if (v) atomicOr(&mb[dg], 1u << lane);
+        __syncwarp();
+        const unsigned peers = v ? mb[dg] : 0u;
+        const int before = v ? (int)my[dg] : 0;
+        __syncwarp();
+        const int r = __popc(peers & lt);
+        pos[k] = before + r;
+        if (v && r == 0) { my[dg] = (uint32_t)(before + __popc(peers)); mb[dg] = 0u; }
+        __syncwarp();
+    }
+    __syncthreads();
+    // Per digit: exclusive scan over the warps, and the tile's count, which is
+    // published at once so that later tiles' look-backs can pass this one.
+    uint32_t cnt = 0;
+    if (t < 256) {
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) {
+            const uint32_t c = whist[ww * 256 + t];
+            whist[ww * 256 + t] = cnt;
+            cnt += c;
+        }
+        st_relaxed_u64(&my_lb[t], (td.tin == 0 ? LB_INC : LB_AGG) | ep | (uint64_t)cnt);
+    }
+    // exclusive scan of the counts over the 256 digits
     {
-        uint32_t dg[ITEMS];
-        bool valid[ITEMS];
-        const int base = w * 32 * ITEMS + lane;
-        if (t < 256) ecount[t] = 0;
-        __syncthreads();
-        // issue every load before the first shared-memory atomic so their
-        // latencies overlap
+        uint32_t tot;
+        const uint32_t ex = ws_block_excl_scan<NT, int>((int)cnt, (int*)mbins, (int*)&tot);
+        if (t < 256) dstart[t] = ex;
+    }
+    __syncthreads();
+    // stage the tile in digit order (frees the key registers before the
+    // look-back)
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            const int p = base + k * 32;
-            valid[k] = p < td.len;
-            if (FIRST) key[k] = valid[k] ? KO::to_key(values[td.vpos + p]) : (K)0;
-            else key[k] = valid[k] ? keys_in[td.kpos + p] : (K)0;
+    for (int k = 0; k < ITEMS; ++k) {
+        if (base + k * 32 < td.len) {
+            const uint32_t dg = (uint32_t)(key[k] >> shift) & 0xffu;
+            skeys[pos[k] + (int)(dstart[dg] + my[dg])] = key[k];
         }
-#pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            dg[k] = (uint32_t)((key[k] >> shift) & 0xff);
-            if (valid[k]) atomicAdd(&ecount[dg[k]], 1u);
-        }
-        __syncthreads();
-        // publish this tile's per-digit counts before the (longer) ranking, so
-        // that later tiles' look-backs do not wait for it
-        if (t < 256) st_relaxed_u64(&my_lb[t], (td.tin == 0 ? LB_INC : LB_AGG) | ep | (uint64_t)ecount[t]);
-        ws_rank_digits<NT, ITEMS, WS_SORT_CHAINS>(dg, valid, pos, whist, dcount, dstart);
     }
 
     // look back over earlier tiles of the segment (windows of 4 predecessors
     // per round trip)
     if (t < 256) {
-        const uint64_t c = dcount[t];
         int64_t gb;   // global position of this digit's first key of the tile, minus its local start
         if (td.tin == 0) {
             gb = 0;
@@ -166,17 +199,10 @@ __global__ void __launch_bounds__(WS_SORT_NT, 4) k_onesweep(const T* __restrict_
                 }
                 if (!done) j -= nwin;
             }
-            st_relaxed_u64(&my_lb[t], LB_INC | ep | (run + c));
+            st_relaxed_u64(&my_lb[t], LB_INC | ep | (run + cnt));
             gb = (int64_t)run;
         }
         gbase[t] = seg_k + (int64_t)dbase[t] + gb - (int64_t)dstart[t];
-    }
-    // stage the tile in digit order
-    {
-        const int base = w * 32 * ITEMS + lane;
-#pragma unroll
-        for (int k = 0; k < ITEMS; ++k)
-            if (base + k * 32 < td.len) skeys[pos[k]] = key[k];
     }
     __syncthreads();
     if (t == 0 && s_timeout) ws_flag(status, WS_STATUS_TIMEOUT);
@@ -185,7 +211,8 @@ __global__ void __launch_bounds__(WS_SORT_NT, 4) k_onesweep(const T* __restrict_
         const int j = t + k * NT;
         if (j < td.len) {
             const K kk = skeys[j];
-            keys_out[gbase[(uint32_t)((kk >> shift) & 0xff)] + j] = kk;
+            const uint32_t dg = (uint32_t)(kk >> shift) & 0xffu;
+            keys_out[gbase[dg] + j] = kk;
         }
     }
 }
@@ -195,7 +222,7 @@ __global__ void __launch_bounds__(WS_SORT_NT, 4) k_onesweep(const T* __restrict_
 template <typename T>
 size_t ws_onesweep_smem() {
     typedef typename KeyOf<T>::K K;
-    return sizeof(K) * WS_SORT_TILE + sizeof(uint32_t) * ((WS_SORT_NT / 32) * WS_SORT_CHAINS * 256 + 2 * 256) +
+    return sizeof(K) * WS_SORT_TILE + sizeof(uint32_t) * (2 * (WS_SORT_NT / 32) * 256 + 256) +
            sizeof(int64_t) * 256;
 }
 
