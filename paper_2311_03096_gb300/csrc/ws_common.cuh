@@ -287,6 +287,26 @@ template <> struct ValueOut<double> {
 // ---------------------------------------------------------------------------
 // Bounded spin-wait helper: every device-side wait has an iteration limit.
 // ---------------------------------------------------------------------------
+// L2 eviction priorities.  The lookup directory is re-read at random by every
+// weight while the weights and outputs stream through L2 once, so the
+// directory is loaded and stored with evict_last and the streams with
+// evict_first (.cs).
+__device__ __forceinline__ uint64_t ws_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint2 ws_ld_u2_last(const void* ptr, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void ws_st_u2_last(void* ptr, uint2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(ptr), "r"(v.x), "r"(v.y), "l"(pol)
+                 : "memory");
+}
+
 __device__ __forceinline__ void ws_backoff(int it) {
     if (it > 64) __nanosleep(it > 4096 ? 256 : 32);
 }

@@ -512,6 +512,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
     const Piece pc = P[tp];
     const int nb = 1 << R.dir_log2;
     DirEntry* D = dir + ls.dir_pos;
+    const uint64_t pol = ws_policy_evict_last();
     auto vertex = [&](int piece_idx, int i, int64_t& pt, i128& X) {
         const Piece q = P[piece_idx];
         size_t v = (size_t)q.tile * (HT + 1) + i;
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
                 gaps[g].key32 = k32;
             } else ws_flag(status, WS_STATUS_INTERNAL);
         } else {
-            for (int64_t bb = from; bb <= to; ++bb) D[bb] = de;
+            for (int64_t bb = from; bb <= to; ++bb) ws_st_u2_last(D + bb, make_uint2((uint32_t)de.idx, de.key32), pol);
         }
         if (r == R.n_clusters - 1) {   // tail: buckets after the last start, plus the sentinel
             int64_t f2 = bcur + 1, c2 = (int64_t)nb - bcur;   // buckets bcur+1 .. nb (nb = sentinel)
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
                     gaps[g].key32 = 0xffffffffu;
                 } else ws_flag(status, WS_STATUS_INTERNAL);
             } else {
-                for (int64_t bb = f2; bb <= nb; ++bb) D[bb] = te;
+                for (int64_t bb = f2; bb <= nb; ++bb) ws_st_u2_last(D + bb, make_uint2((uint32_t)te.idx, te.key32), pol);
             }
         }
     }
@@ -578,10 +579,11 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
 __global__ void __launch_bounds__(256) k_big_gaps(const BigGap* gaps, const uint32_t* ngaps, DirEntry* dir,
                                                   int64_t gap_cap) {
     const int64_t n = min((int64_t)*ngaps, gap_cap);
+    const uint64_t pol = ws_policy_evict_last();
     for (int64_t g = blockIdx.x; g < n; g += gridDim.x) {
         const BigGap G = gaps[g];
         const DirEntry e{G.value, G.key32};
-        for (int i = threadIdx.x; i < G.count; i += 256) dir[G.pos + i] = e;
+        for (int i = threadIdx.x; i < G.count; i += 256) ws_st_u2_last(dir + G.pos + i, make_uint2((uint32_t)e.idx, e.key32), pol);
     }
 }
 
@@ -631,6 +633,7 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
     const DirEntry* D = dir + ls.dir_pos;
     const CEntry<T>* tab = table + R.table_pos;
     const int c = (int)R.n_clusters;
+    const uint64_t pol = ws_policy_evict_last();
     for (int i0 = threadIdx.x; i0 < td.len; i0 += 256 * LK) {
         T x[LK];
         K k[LK];
@@ -641,14 +644,15 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
         for (int u = 0; u < LK; ++u) {
             const int i = i0 + u * 256;
             in[u] = i < td.len;
-            x[u] = in[u] ? values[td.vpos + i] : (T)0;
+            x[u] = in[u] ? __ldcs(values + td.vpos + i) : (T)0;
         }
 #pragma unroll
         for (int u = 0; u < LK; ++u) {
             k[u] = KO::to_key(x[u]);
             const int b = ws_bucket((float)x[u], R.lo, R.scale, nb);
-            e0[u] = D[b];
-            e1[u] = D[b + 1];
+            const uint2 a0 = ws_ld_u2_last(D + b, pol), a1 = ws_ld_u2_last(D + b + 1, pol);
+            e0[u] = DirEntry{(int32_t)a0.x, a0.y};
+            e1[u] = DirEntry{(int32_t)a1.x, a1.y};
         }
 #pragma unroll
         for (int u = 0; u < LK; ++u) {
@@ -684,8 +688,8 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
             if (r < 0 || r >= c) { ws_flag(status, WS_STATUS_INTERNAL); r = 0; ce = tab[0]; }
             if (in[u]) {
                 const int i = i0 + u * 256;
-                out[td.vpos + i] = ce.val;
-                if (ids) ids[td.vpos + i] = r;
+                __stcs(out + td.vpos + i, ce.val);
+                if (ids) __stcs(ids + td.vpos + i, r);
             }
         }
     }
