@@ -175,6 +175,148 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _time_calls(fn, stream, reps):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _oracle_segments(args):
+    import oracle
+
+    vals, off, lam = args
+    for s in range(len(lam)):
+        oracle.prox(vals[off[s]:off[s + 1]], float(lam[s]))
+    return int(off[-1])
+
+
+def bench_batched(ws, ctx, stream, reps=5):
+    """Batched MLP layout (rows, whole layers, 4096 log-uniform extras): elements/s
+    of each set and of all of them in one call (eager and CUDA-graph replay),
+    errors against the oracle on sampled segments, and the oracle run
+    segment-parallel over the host cores on a bounded sample."""
+    import multiprocessing as mp
+    import os
+
+    import torch
+
+    import oracle
+    from paper_2311_03096_gb300 import inputs
+
+    vals, off, lam, kinds = inputs.batched_segments(seed=0)
+    kinds = np.asarray(kinds)
+    res = {"elements": int(off[-1]), "segments": int(len(lam))}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for name, sel in (("rows", kinds == "row"), ("layers", kinds == "layer"), ("extras", kinds == "extra"),
+                      ("all", np.ones(len(kinds), bool))):
+        idx = np.nonzero(sel)[0]
+        lens = np.diff(off)[idx]
+        sub_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        sub_vals = vals if name == "all" else np.concatenate([vals[off[s]:off[s + 1]] for s in idx])
+        plan = ws.Plan(sub_off, torch.float32, ctx=ctx)
+        v = torch.from_numpy(sub_vals).to(dev)
+        lt = torch.from_numpy(lam[idx]).to(dev)
+        out = torch.empty_like(v)
+        ids = torch.empty(v.shape[0], dtype=torch.int32, device=dev)
+        nc = torch.zeros(len(idx), dtype=torch.int64, device=dev)
+        run = lambda: plan.forward(v, lt, "fp32comp", out=out, id_out=ids, n_clusters=nc, stream=stream)  # noqa: E731
+        ms = _time_calls(run, stream, reps)
+        entry = {"elements": int(sub_off[-1]), "segments": int(len(idx)), "ms": ms,
+                 "elements_per_s": sub_off[-1] / (ms / 1e3)}
+        if name == "all":
+            g = torch.cuda.CUDAGraph()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                run_g = lambda: plan.forward(v, lt, "fp32comp", out=out, id_out=ids, n_clusters=nc)  # noqa: E731
+                run_g()
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g):
+                run_g()
+            msg = _time_calls(g.replay, stream, reps)
+            entry["graph_ms"] = msg
+            entry["graph_elements_per_s"] = sub_off[-1] / (msg / 1e3)
+            ctx.check(what="bench batched")
+            out_h, ids_h = out.cpu().numpy(), ids.cpu().numpy()
+            rng = np.random.default_rng(7)
+            pick = list(np.nonzero(kinds == "layer")[0]) + list(rng.choice(np.nonzero(kinds == "row")[0], 8)) + \
+                list(rng.choice(np.nonzero(kinds == "extra")[0], 8))
+            worst, same = 0.0, True
+            for s in pick:
+                a, b = off[s], off[s + 1]
+                ref, rid, _ = oracle.prox(vals[a:b], float(lam[s]))
+                scale = float(np.abs(vals[a:b]).max()) + float(lam[s])
+                worst = max(worst, float(np.abs(out_h[a:b].astype(np.float64) - ref).max()) / scale)
+                same &= bool(np.array_equal(ids_h[a:b], rid))
+            entry["error_vs_oracle_sampled"] = {"segments": len(pick), "max_err_rel_to_max_w_plus_lambda": worst,
+                                                "partition_equal": same}
+        res[name] = entry
+        del plan, v, lt, out, ids, nc
+        torch.cuda.empty_cache()
+    ctx.check(what="bench batched")
+    # the oracle over all host cores (one segment per task), on rows + layers + the first extras
+    cores = os.cpu_count() or 1
+    extra_idx = np.nonzero(kinds == "extra")[0]
+    take = [s for s in range(len(lam)) if kinds[s] != "extra"] + list(extra_idx[:256])
+    chunks = [[] for _ in range(cores)]
+    for j, s in enumerate(sorted(take, key=lambda s: -(off[s + 1] - off[s]))):
+        chunks[j % cores].append(s)
+    tasks = []
+    for c in chunks:
+        if not c:
+            continue
+        lens = np.array([off[s + 1] - off[s] for s in c], np.int64)
+        sub_off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+        tasks.append((np.concatenate([vals[off[s]:off[s + 1]] for s in c]), sub_off, lam[c]))
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(len(tasks)) as pool:
+        n = sum(pool.map(_oracle_segments, tasks))
+    dt = time.time() - t0
+    res["oracle_parallel"] = {"value": n / dt, "unit": "elements/s", "cores": len(tasks), "kind": "oracle",
+                              "sample": f"{len(take)} segments (all rows, all layers, 256 extras; {n} elements), "
+                                        f"{dt:.1f} s including process start"}
+    return res
+
+
+def bench_train(ws, ctx, stream, steps=10):
+    """Proximal SGD step on the MLP (batch 256 of 32x32x3): ms per step and the prox share."""
+    import torch
+
+    from paper_2311_03096_gb300 import inputs
+    from paper_2311_03096_gb300.train import ProxMLP
+
+    m = ProxMLP(seed=0)
+    x_np, y_np = inputs.images(batch=256, seed=0)
+    x, y = torch.from_numpy(x_np).cuda(), torch.from_numpy(y_np).cuda()
+    for _ in range(3):
+        m.step(x, y)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
+    for k in range(steps):
+        ev[3 * k].record(stream)
+        m.sgd(x, y)
+        ev[3 * k + 1].record(stream)
+        m.prox(stream=stream)
+        ev[3 * k + 2].record(stream)
+    torch.cuda.synchronize()
+    ctx.check(what="bench train")
+    step = sum(ev[3 * k].elapsed_time(ev[3 * k + 2]) for k in range(steps)) / steps
+    prox = sum(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(steps)) / steps
+    return {"ms_per_step": step, "prox_ms": prox, "prox_share": prox / step,
+            "rows": int(m.offsets.shape[0] - 1), "weights": int(m.flat.shape[0]), "batch": 256,
+            "lr": m.lr, "alpha": m.alpha}
+
+
 def config_dict(args, world):
     return {"workload": WORKLOAD, "d": args.d, "lambdas": list(LAMBDAS), "storage": "f32", "prec": args.prec,
             "seed": args.seed, "l2": "inputs larger than L2 (256 MiB vector per step)",
@@ -366,6 +508,8 @@ def main():
                 same = bool(np.array_equal(i.cpu().numpy(), ref_ids))
                 errs[f"{prec}_lam{lam:g}"] = {"max_err_rel_to_max_w_plus_lambda": err, "partition_equal": same}
         variants["error_vs_oracle_2^20"] = errs
+        variants["batched_mlp"] = bench_batched(ws, ctx, stream)
+        variants["train_step"] = bench_train(ws, ctx, stream)
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample
     cpu = None
