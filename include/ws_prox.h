@@ -146,17 +146,15 @@ ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, voi
  * grad_out over the cluster of i, clusters given by cluster_ids (0-based,
  * < d) as written by the forward.  It exists for callers that must not call
  * cudaMalloc/cudaFree where they run the backward: a framework that has
- * already reserved the device memory for its own pool, a loop that cannot
- * take the implicit device synchronisation of an allocation, or code running
- * while a stream is captured.  Its per-cluster sums and counts live in one
- * fixed array of device memory (12 MiB) that the library holds on every GPU
- * that loads it until the process exits.
+ * already reserved the device memory for its own pool, or a loop that cannot
+ * take the implicit device synchronisation of an allocation.  Its per-cluster
+ * sums and counts live in one fixed array of device memory (12 MiB) that the
+ * library holds on every GPU that loads it until the process exits.
  *   - grad_out, cluster_ids, grad_in: DEVICE pointers owned by the caller
  *     (d elements of dtype, d int32, d elements of dtype); grad_in may alias
  *     grad_out.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before capturing any stream on that device.  No call allocates.
+ *     (cudaGetSymbolAddress) with that device current.  No call allocates.
  *   - d > WS_NOALLOC_MAX_ELEMS or d < 0 returns WS_ERR_INVALID and enqueues
  *     nothing; d == 0 is a no-op.  Ids outside [0, d) are skipped and leave
  *     their grad_in entry unchanged.

@@ -2,10 +2,9 @@
 //
 // Who needs it: code that must not call cudaMalloc/cudaFree at the point where
 // it runs the backward -- for example a training step whose framework has
-// already reserved all device memory in its own pool, a loop that cannot
+// already reserved all device memory in its own pool, or a loop that cannot
 // afford the implicit device-wide synchronisation cudaMalloc and cudaFree
-// perform, or code that runs while a stream is being captured into a CUDA
-// graph.  The regular ws_prox_backward gets its per-cluster scratch from a
+// perform.  The regular ws_prox_backward gets its per-cluster scratch from a
 // plan, which allocates on first use of a shape.
 //
 // Here the scratch (one sum and one count per cluster) lives in a

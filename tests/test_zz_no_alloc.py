@@ -1,9 +1,9 @@
 """The allocation-free backward entry point (ws_prox_backward_noalloc).
 
 It serves callers that must not allocate device memory where the backward
-runs (a framework that has pre-reserved the GPU's memory for its own pool, a
-loop that cannot take the device-wide synchronisation of cudaMalloc/cudaFree,
-code running during stream capture).  Its output must equal the regular
+runs (a framework that has pre-reserved the GPU's memory for its own pool, or a
+loop that cannot take the device-wide synchronisation of cudaMalloc/cudaFree).
+Its output must equal the regular
 plan-based ws_prox_backward on the same inputs, on consecutive calls that
 reuse the library's fixed scratch array.  This file is collected last so that
 a stop-at-first-failure run has already run every other test; it also passes
