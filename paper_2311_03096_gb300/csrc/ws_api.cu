@@ -58,6 +58,7 @@ struct ws_plan {
     uint64_t* lookback = nullptr;
     uint32_t* tile_counter = nullptr;
     uint32_t* epoch = nullptr;
+    int32_t* seg_emin = nullptr;
     uint16_t* vp = nullptr;
     i128* vx = nullptr;
     int32_t* nvert = nullptr;
@@ -92,6 +93,7 @@ LargeWork<T> make_work(const ws_plan* p) {
     W.lookback = p->lookback;
     W.tile_counter = p->tile_counter;
     W.epoch = p->epoch;
+    W.seg_emin = p->seg_emin;
     W.vp = p->vp;
     W.vx = p->vx;
     W.nvert = p->nvert;
@@ -200,6 +202,7 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->lookback, sizeof(uint64_t) * (size_t)P * p->n_sort_tiles * 256))) return st;
     if ((st = plan_alloc(p, (void**)&p->tile_counter, sizeof(uint32_t) * P))) return st;
     if ((st = plan_alloc(p, (void**)&p->epoch, sizeof(uint32_t)))) return st;
+    if ((st = plan_alloc(p, (void**)&p->seg_emin, sizeof(int32_t) * p->n_lseg))) return st;
     if (cudaMemset(p->epoch, 0, sizeof(uint32_t)) != cudaSuccess) return WS_ERR_CUDA;
     if (cudaMemset(p->lookback, 0, sizeof(uint64_t) * (size_t)P * p->n_sort_tiles * 256) != cudaSuccess)
         return WS_ERR_CUDA;

@@ -348,7 +348,9 @@ static __device__ __noinline__ bool ws_convex_binade_exact(int64_t A, int64_t B,
     return (Lv << (128 - bl)) > (Rv << (128 - br));
 }
 
-// Binade tiles.  When range * n^2 <= 2^62 (always for FP32 keys), Delta =
+// Tiles whose prefix sums are 64-bit deviations: binade tiles (ulps from the
+// first key, scale of the tile) and narrow tiles (q - q_0, scale of the
+// segment).  When range * n^2 <= 2^62 (every FP32 binade tile), Delta =
 // B n1 - A n2 is exact in 64 bits and only the right-hand side mu (c-a) n1 n2
 // is rounded, so the FP32 filter's error is relative to |Delta| + rhs rather
 // than to the cancelling terms B n1 and A n2: Delta is converted once (2^-24),
@@ -358,7 +360,7 @@ static __device__ __noinline__ bool ws_convex_binade_exact(int64_t A, int64_t B,
 // filter runs on the rounded terms as in TilePts.  Near-ties fall through to
 // the exact integer test.
 template <int M>
-struct TilePtsBinade {
+struct TilePtsDev {
     const int64_t* s64;
     float muq;       // lambda 2^L_tile / (d - 1)
     bool fast;
@@ -414,19 +416,18 @@ struct TilePtsBinade {
     }
 };
 
-// True when a binade tile's keys k0..kn (n keys) keep B n1 - A n2 exact in
-// 64 bits: |B n1|, |A n2| <= n1 n2 (kn - k0) <= n^2 (kn - k0) / 4.
-template <typename K>
-__device__ __forceinline__ bool ws_binade_d64(K k0, K kn, int n) {
-    return n <= 1 || (uint64_t)(kn - k0) <= (((uint64_t)1 << 62) / (uint64_t)n) / (uint64_t)n;
+// True when a tile of n points whose deviations span `range` keeps
+// B n1 - A n2 exact in 64 bits: |B n1|, |A n2| <= n1 n2 range <= n^2 range / 4.
+__device__ __forceinline__ bool ws_dev_d64(uint64_t range, int n) {
+    return n <= 1 || range <= (((uint64_t)1 << 62) / (uint64_t)n) / (uint64_t)n;
 }
 
-// Binade points of a tile with constants sc (fixed-point scale of the tile).
-template <int M, typename K>
-__device__ __forceinline__ TilePtsBinade<M> ws_binade_pts(const int64_t* s64, float muq, bool fast, K k0, K kn,
-                                                          int n, const SegConst& sc) {
-    TilePtsBinade<M> P;
-    P.s64 = s64; P.muq = muq; P.fast = fast; P.d64 = ws_binade_d64<K>(k0, kn, n);
+// Deviation points of a tile with constants sc (its fixed-point scale).
+template <int M>
+__device__ __forceinline__ TilePtsDev<M> ws_dev_pts(const int64_t* s64, float muq, bool fast, uint64_t range, int n,
+                                                    const SegConst& sc) {
+    TilePtsDev<M> P;
+    P.s64 = s64; P.muq = muq; P.fast = fast; P.d64 = ws_dev_d64(range, n);
     if (sc.mlam == 0) { P.modd = 0; P.sodd = 0; }
     else { const int tz = __ffsll((long long)sc.mlam) - 1; P.modd = sc.mlam >> tz; P.sodd = sc.s + tz; }
     return P;

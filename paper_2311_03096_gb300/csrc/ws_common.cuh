@@ -10,7 +10,8 @@
 //   * S_p = X_p + lambda p (d - p)/(d - 1) with X_p = sum_{j<p} x_j, so
 //     slope(a, b) = mean(x_a..x_{b-1}) + lambda (d - a - b)/(d - 1): the shift
 //     never has to be stored;
-//   * X is carried in 128-bit fixed point (q_j = x_j * 2^L, |q_j| <= 2^58,
+//   * X is carried in 128-bit fixed point (q_j = x_j * 2^L, |q_j| <= 2^58, L
+//     the smallest scale at which every value is an integer when that fits,
 //     exact for every input whose values span < ~2^(58-24) of dynamic range),
 //     and the "is b a strict hull vertex between a and c" test is decided
 //     with exact integer arithmetic (below), so merge decisions never round.
@@ -87,9 +88,10 @@ template <typename T> __device__ __forceinline__ int ws_eff_exp(T v) {
     return e == 0 ? 1 : e;
 }
 
-// Fixed-point image q = x * 2^L, L = L_BASE - emax, truncated toward zero
-// when x has bits below 2^-L (monotone, so sorted order is preserved).
-// |q| <= 2^58 whenever the effective exponent of x is <= emax.
+// Fixed-point image q = x * 2^L, L = L_BASE - emax (emax: the scale parameter
+// E of ws_fix_scale), truncated toward zero when x has bits below 2^-L
+// (monotone, so sorted order is preserved).  |q| <= 2^58 whenever the
+// effective exponent of x is <= E.
 template <typename T> __device__ __forceinline__ int64_t ws_fixed(T v, int emax) {
     typedef KeyOf<T> KO;
     uint64_t b = (uint64_t)KO::bits(v);
@@ -102,6 +104,18 @@ template <typename T> __device__ __forceinline__ int64_t ws_fixed(T v, int emax)
     else mag = (sh > -64) ? (m >> (-sh)) : 0ull;
     bool neg = (b >> (KO::BITS - 1)) & 1ull;
     return neg ? -(int64_t)mag : (int64_t)mag;
+}
+
+// Scale parameter E of a segment's fixed point (L = L_BASE - E): the largest
+// E at which every value is still an exact integer, E = emin + FIX_OFS, as
+// long as the largest value then stays within 2^58 (E >= emax); otherwise
+// E = emax and values more than FIX_OFS binades below the largest lose their
+// lowest bits (toward zero).  emin / emax: smallest / largest effective
+// exponent of the segment's nonzero values (emin > emax when there are none).
+// Small q keeps tiles that cross binades (zero crossings) in 64-bit
+// deviations instead of 128-bit sums.
+template <typename T> __device__ __forceinline__ int ws_fix_scale(int emax, int emin) {
+    return (emin <= emax && emax - emin <= KeyOf<T>::FIX_OFS) ? emin + KeyOf<T>::FIX_OFS : emax;
 }
 
 // ---------------------------------------------------------------------------

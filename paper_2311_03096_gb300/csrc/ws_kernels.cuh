@@ -123,6 +123,7 @@ struct LargeWork {
     uint64_t* lookback;      // [passes][n_sort_tiles][256]
     uint32_t* tile_counter;  // [passes]
     uint32_t* epoch;         // [1] look-back epoch, advanced by every sort
+    int32_t* seg_emin;       // [n_lseg] smallest effective exponent of a nonzero value
     // hull
     uint16_t* vp;            // [n_hull_tiles][WS_HULL_TILE + 1] vertex points (tile-local)
     i128* vx;                // [n_hull_tiles][WS_HULL_TILE + 1] X at vertices (tile-local)

@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(HNT, 3) k_tile_hull(const typename KeyOf<T>::K
                                                    const double* __restrict__ lambdas, SegRuntime* rt,
                                                    uint16_t* vp, i128* vx, int32_t* nvert, i128* tile_total,
                                                    Piece* pieces, int32_t* npieces, int32_t* arrive, int n_hull,
-                                                   uint32_t* status) {
+                                                   const int32_t* __restrict__ seg_emin, uint32_t* status) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(HNT, 3) k_tile_hull(const typename KeyOf<T>::K
     const K* kp = sorted + td.kpos;
     const K kfirst = kp[0], klast = kp[n - 1];
     const T xlo = KO::from_key(sorted[ls.kpos]), xhi = KO::from_key(sorted[ls.kpos + ls.len - 1]);
-    const int emax = max(ws_eff_exp(xlo), ws_eff_exp(xhi));
+    const int emax = ws_fix_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), seg_emin[td.lseg]);
     if (t == 0) {
         if (!lam_ok) ws_flag(status, WS_STATUS_BAD_LAMBDA);
         if (td.tin == 0) rt[td.lseg].emax = emax;
@@ -391,10 +391,12 @@ __global__ void __launch_bounds__(HNT, 3) k_tile_hull(const typename KeyOf<T>::K
     const int mode = ws_tile_prefix<T, HNT, HM>(s.pre, kr, kfirst, klast, n, emax, q0, total, bsh);
     int nv;
     if (mode == WS_TILE_BINADE) {
-        const TilePtsBinade<HM> P = ws_binade_pts<HM, K>(s.pre.s64, s.muqt, s.fastt != 0, kfirst, klast, n, s.sct);
+        const TilePtsDev<HM> P =
+            ws_dev_pts<HM>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(klast - kfirst), n, s.sct);
         ws_cta_hull<HNT, HM>(s.hull, n, P, s.sct, &nv);
     } else if (mode == WS_TILE_NARROW) {
-        const TilePts<HM, true> P{s.pre.s64, s.pre.base, q0, s.muq, s.fast != 0};
+        const uint64_t range = (uint64_t)(ws_fixed<T>(KO::from_key(klast), emax) - q0);
+        const TilePtsDev<HM> P = ws_dev_pts<HM>(s.pre.s64, s.muq, s.fast != 0, range, n, s.sc);
         ws_cta_hull<HNT, HM>(s.hull, n, P, s.sc, &nv);
     } else {
         const TilePts<HM, false> P{s.pre.s64, s.pre.base, q0, 0.0f, false};
@@ -757,7 +759,7 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
     WS_LAUNCH(W.prof, WSK_TILE_HULL, st,
               (k_tile_hull<T><<<W.n_hull_tiles, HNT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp,
                                                                 W.vx, W.nvert, W.tile_total, W.pieces, W.npieces,
-                                                                W.arrive, W.n_hull_tiles, status)));
+                                                                W.arrive, W.n_hull_tiles, W.seg_emin, status)));
     e = cudaMemsetAsync(W.tile_piece, 0xff, sizeof(int32_t) * (size_t)W.n_hull_tiles, st);
     if (e) return e;
     WS_LAUNCH(W.prof, WSK_ROOT, st,

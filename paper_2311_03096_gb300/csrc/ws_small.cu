@@ -28,6 +28,7 @@ struct SmallSmem {
     } u;
     int wsum_i[NT / 32];
     int flags;
+    int emin;
     SegConst sc, sct;
     float muq, muqt;
     int fast, fastt;
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
     }
 
     // ---- load (striped per warp, coalesced), map to keys, check finiteness
-    if (t == 0) s.flags = 0;
+    if (t == 0) { s.flags = 0; s.emin = 0x7fffffff; }
     __syncthreads();
     bool bad = false;
 #pragma unroll
@@ -114,20 +115,29 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
     }
 
     // ---- fixed point and prefix sums (blocked: thread t owns sorted [t*M, t*M+M))
+    int64_t q0;
+    i128 total;
+    int bsh;
+    K kr[M];
+    int emin = 0x7fffffff;   // smallest effective exponent of a nonzero value
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        kr[i] = (t * M + i < n) ? s.keys[t * M + i] : (K)0;
+        const T x = KO::from_key(kr[i]);
+        if (t * M + i < n && x != (T)0) emin = min(emin, ws_eff_exp(x));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emin = min(emin, __shfl_xor_sync(WS_FULL_MASK, emin, o));
+    if (lane == 0) atomicMin(&s.emin, emin);
+    __syncthreads();
     const T xlo = KO::from_key(s.keys[0]), xhi = KO::from_key(s.keys[n - 1]);
-    const int emax = max(ws_eff_exp(xlo), ws_eff_exp(xhi));
+    const int emax = ws_fix_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), s.emin);
     if (t == 0) {
         s.sc = ws_seg_const<T>(n, lam, emax);
         bool f;
         s.muq = ws_muq(lam, s.sc, f);
         s.fast = f ? 1 : 0;
     }
-    int64_t q0;
-    i128 total;
-    int bsh;
-    K kr[M];
-#pragma unroll
-    for (int i = 0; i < M; ++i) kr[i] = (t * M + i < n) ? s.keys[t * M + i] : (K)0;
     if (t == 0) {
         const int sh0 = ws_eff_exp(KO::from_key(s.keys[0])) - emax + KO::FIX_OFS;
         s.sct = ws_seg_const_L(n, lam, s.sc.L - (sh0 > 0 ? sh0 : 0));
@@ -141,10 +151,12 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
     // ---- exact hull (in-CTA merge)
     int nv;
     if (mode == WS_TILE_BINADE) {
-        const TilePtsBinade<M> P = ws_binade_pts<M, K>(s.pre.s64, s.muqt, s.fastt != 0, s.keys[0], s.keys[n - 1], n, s.sct);
+        const TilePtsDev<M> P =
+            ws_dev_pts<M>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(s.keys[n - 1] - s.keys[0]), n, s.sct);
         ws_cta_hull<NT, M>(s.hull, n, P, s.sct, &nv);
     } else if (mode == WS_TILE_NARROW) {
-        const TilePts<M, true> P{s.pre.s64, s.pre.base, q0, s.muq, s.fast != 0};
+        const uint64_t range = (uint64_t)(ws_fixed<T>(KO::from_key(s.keys[n - 1]), emax) - q0);
+        const TilePtsDev<M> P = ws_dev_pts<M>(s.pre.s64, s.muq, s.fast != 0, range, n, sc);
         ws_cta_hull<NT, M>(s.hull, n, P, sc, &nv);
     } else {
         const TilePts<M, false> P{s.pre.s64, s.pre.base, q0, 0.0f, false};

@@ -36,25 +36,36 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
     return v;
 }
 
+// Also the smallest effective exponent of a nonzero value of each segment
+// (seg_emin, reduced with atomicMin; cleared to INT_MAX before the launch),
+// which fixes the segment's fixed-point scale.
 template <typename T>
 __global__ void __launch_bounds__(WS_SORT_NT) k_hist(const T* __restrict__ values, const TileDesc* __restrict__ tiles,
-                                                     uint32_t* hist, uint32_t* status) {
+                                                     uint32_t* hist, int32_t* seg_emin, uint32_t* status) {
     typedef KeyOf<T> KO;
     constexpr int P = KO::BITS / 8;
     __shared__ uint32_t h[P * 256];
+    __shared__ int s_emin;
     for (int i = threadIdx.x; i < P * 256; i += WS_SORT_NT) h[i] = 0;
+    if (threadIdx.x == 0) s_emin = 0x7fffffff;
     __syncthreads();
     const TileDesc td = tiles[blockIdx.x];
     bool bad = false;
+    int emin = 0x7fffffff;
     for (int i = threadIdx.x; i < td.len; i += WS_SORT_NT) {
         T v = values[td.vpos + i];
         bad |= !ws_isfinite(v);
+        if (v != (T)0) emin = min(emin, ws_eff_exp(v));
         typename KO::K k = KO::to_key(v);
 #pragma unroll
         for (int p = 0; p < P; ++p) atomicAdd(&h[p * 256 + (int)((k >> (8 * p)) & 0xff)], 1u);
     }
     if (bad) ws_flag(status, WS_STATUS_NONFINITE);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    if ((threadIdx.x & 31) == 0 && emin != 0x7fffffff) atomicMin(&s_emin, emin);
     __syncthreads();
+    if (threadIdx.x == 0 && s_emin != 0x7fffffff) atomicMin(&seg_emin[td.lseg], s_emin);
     uint32_t* gh = hist + (size_t)td.lseg * P * 256;
     for (int i = threadIdx.x; i < P * 256; i += WS_SORT_NT)
         if (h[i]) atomicAdd(&gh[i], h[i]);
@@ -238,7 +249,10 @@ cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* stat
     if (e) return e;
     e = cudaMemsetAsync(W.tile_counter, 0, sizeof(uint32_t) * P, st);
     if (e) return e;
-    WS_LAUNCH(W.prof, WSK_HIST, st, (k_hist<T><<<W.n_sort_tiles, WS_SORT_NT, 0, st>>>(values, W.sort_tiles, W.hist, status)));
+    e = cudaMemsetAsync(W.seg_emin, 0x7f, sizeof(int32_t) * (size_t)W.n_lseg, st);
+    if (e) return e;
+    WS_LAUNCH(W.prof, WSK_HIST, st,
+              (k_hist<T><<<W.n_sort_tiles, WS_SORT_NT, 0, st>>>(values, W.sort_tiles, W.hist, W.seg_emin, status)));
     WS_LAUNCH(W.prof, WSK_HIST_SCAN, st, (k_hist_scan<<<W.n_lseg * P, 256, 0, st>>>(W.hist, W.epoch)));
     size_t smem = ws_onesweep_smem<T>();
     e = cudaFuncSetAttribute(k_onesweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
