@@ -7,25 +7,32 @@
 
 namespace {
 
+// Shared memory of one segment, laid out so that three CTAs fit on an SM:
+// buffers whose lifetimes do not overlap share storage.
+//   r1: digit counters of the sort  |  hull vertex list + cluster-start bits
+//   r2: sort keys (dead after the prefix sums)  |  chunk hulls  |  values
 template <typename T, int NT, int M>
 struct SmallSmem {
     typedef typename KeyOf<T>::K K;
     static constexpr int CAP = NT * M;
-    K keys[CAP];
+    static_assert(32 % M == 0 || M % 32 == 0, "a thread's marks must lie in one 32-bit word");
     uint16_t idx[CAP];
     TilePrefix<NT, M> pre;  // fixed-point prefix sums of the sorted segment
-    HullSmem<NT, M> hull;
-    uint16_t V[CAP + 1];    // hull vertices (points)
     union {
         struct {
             uint32_t whist[(NT / 32) * 256];
             uint32_t dcount[256], dstart[256];
         } sort;
         struct {
-            T val[CAP];
-            uint8_t mark[CAP];
-        } out;
-    } u;
+            uint16_t V[CAP + 2];        // hull vertices (points)
+            uint32_t mark[CAP / 32];    // bit p: a cluster starts at sorted position p
+        } ids;
+    } r1;
+    union {
+        K keys[CAP];
+        HullSmem<NT, M> hull;
+        T val[CAP];
+    } r2;
     int wsum_i[NT / 32];
     int flags;
     int emin;
@@ -35,7 +42,7 @@ struct SmallSmem {
 };
 
 template <typename T, int NT, int M>
-__global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, const int64_t* __restrict__ offsets,
+__global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, const int64_t* __restrict__ offsets,
                                               const int32_t* __restrict__ seg_list, const double* __restrict__ lambdas,
                                               T* out, int32_t* ids, int64_t* n_clusters, int fp64,
                                               uint32_t* status) {
@@ -72,7 +79,7 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
         if (p < n) {
             T v = values[a0 + p];
             bad |= !ws_isfinite(v);
-            s.keys[p] = KO::to_key(v);
+            s.r2.keys[p] = KO::to_key(v);
             s.idx[p] = (uint16_t)p;
         }
     }
@@ -102,15 +109,15 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
         for (int k = 0; k < ITEMS; ++k) {
             int p = w * 32 * ITEMS + k * 32 + lane;
             valid[k] = p < n;
-            kk[k] = valid[k] ? s.keys[p] : (K)0;
+            kk[k] = valid[k] ? s.r2.keys[p] : (K)0;
             ii[k] = valid[k] ? s.idx[p] : (uint16_t)0;
             dg[k] = (uint32_t)((kk[k] >> (8 * pass)) & 0xff);
         }
         __syncthreads();
-        ws_rank_digits<NT, ITEMS, 1>(dg, valid, pos, s.u.sort.whist, s.u.sort.dcount, s.u.sort.dstart);
+        ws_rank_digits<NT, ITEMS, 1>(dg, valid, pos, s.r1.sort.whist, s.r1.sort.dcount, s.r1.sort.dstart);
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k)
-            if (valid[k]) { s.keys[pos[k]] = kk[k]; s.idx[pos[k]] = ii[k]; }
+            if (valid[k]) { s.r2.keys[pos[k]] = kk[k]; s.idx[pos[k]] = ii[k]; }
         __syncthreads();
     }
 
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
     int emin = 0x7fffffff;   // smallest effective exponent of a nonzero value
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        kr[i] = (t * M + i < n) ? s.keys[t * M + i] : (K)0;
+        kr[i] = (t * M + i < n) ? s.r2.keys[t * M + i] : (K)0;
         const T x = KO::from_key(kr[i]);
         if (t * M + i < n && x != (T)0) emin = min(emin, ws_eff_exp(x));
     }
@@ -130,7 +137,8 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
     for (int o = 16; o > 0; o >>= 1) emin = min(emin, __shfl_xor_sync(WS_FULL_MASK, emin, o));
     if (lane == 0) atomicMin(&s.emin, emin);
     __syncthreads();
-    const T xlo = KO::from_key(s.keys[0]), xhi = KO::from_key(s.keys[n - 1]);
+    const K kfirst = s.r2.keys[0], klast = s.r2.keys[n - 1];
+    const T xlo = KO::from_key(kfirst), xhi = KO::from_key(klast);
     const int emax = ws_fix_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), s.emin);
     if (t == 0) {
         s.sc = ws_seg_const<T>(n, lam, emax);
@@ -139,60 +147,60 @@ __global__ void __launch_bounds__(NT) k_small(const T* __restrict__ values, cons
         s.fast = f ? 1 : 0;
     }
     if (t == 0) {
-        const int sh0 = ws_eff_exp(KO::from_key(s.keys[0])) - emax + KO::FIX_OFS;
+        const int sh0 = ws_eff_exp(xlo) - emax + KO::FIX_OFS;
         s.sct = ws_seg_const_L(n, lam, s.sc.L - (sh0 > 0 ? sh0 : 0));
         bool f;
         s.muqt = ws_muq(lam, s.sct, f);
         s.fastt = f ? 1 : 0;
     }
-    const int mode = ws_tile_prefix<T, NT, M>(s.pre, kr, s.keys[0], s.keys[n - 1], n, emax, q0, total, bsh);
+    // (the prefix sums end with a barrier; the keys' storage is reused from here on)
+    const int mode = ws_tile_prefix<T, NT, M>(s.pre, kr, kfirst, klast, n, emax, q0, total, bsh);
     const SegConst& sc = s.sc;
 
     // ---- exact hull (in-CTA merge)
     int nv;
     if (mode == WS_TILE_BINADE) {
         const TilePtsDev<M> P =
-            ws_dev_pts<M>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(s.keys[n - 1] - s.keys[0]), n, s.sct);
-        ws_cta_hull<NT, M>(s.hull, n, P, s.sct, &nv);
+            ws_dev_pts<M>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(klast - kfirst), n, s.sct);
+        ws_cta_hull<NT, M>(s.r2.hull, n, P, s.sct, &nv);
     } else if (mode == WS_TILE_NARROW) {
-        const uint64_t range = (uint64_t)(ws_fixed<T>(KO::from_key(s.keys[n - 1]), emax) - q0);
+        const uint64_t range = (uint64_t)(ws_fixed<T>(xhi, emax) - q0);
         const TilePtsDev<M> P = ws_dev_pts<M>(s.pre.s64, s.muq, s.fast != 0, range, n, sc);
-        ws_cta_hull<NT, M>(s.hull, n, P, sc, &nv);
+        ws_cta_hull<NT, M>(s.r2.hull, n, P, sc, &nv);
     } else {
         const TilePts<M, false> P{s.pre.s64, s.pre.base, q0, 0.0f, false};
-        ws_cta_hull<NT, M>(s.hull, n, P, sc, &nv);
+        ws_cta_hull<NT, M>(s.r2.hull, n, P, sc, &nv);
     }
     auto X = [&](int p) -> i128 { return ws_tile_X<M>(s.pre.s64, s.pre.base, mode, q0, bsh, p); };
     {
-        int l = s.hull.lo[t], h = s.hull.hi[t], o = s.hull.cum[t];
-        for (int i = l; i < h; ++i) s.V[o + (i - l)] = s.hull.H[i * NT + t];
+        int l = s.r2.hull.lo[t], h = s.r2.hull.hi[t], o = s.r2.hull.cum[t];
+        for (int i = l; i < h; ++i) s.r1.ids.V[o + (i - l)] = s.r2.hull.H[i * NT + t];
     }
-    for (int p = t; p < n; p += NT) s.u.out.mark[p] = 0;
-    __syncthreads();
+    for (int i = t; i < CAP / 32; i += NT) s.r1.ids.mark[i] = 0u;
+    __syncthreads();   // the chunk hulls are dead from here on (their storage holds the values)
     const int c = nv - 1;
-    if (s.V[0] != 0 || s.V[c] != n) { if (t == 0) ws_flag(status, WS_STATUS_INTERNAL); }
+    if (s.r1.ids.V[0] != 0 || s.r1.ids.V[c] != n) { if (t == 0) ws_flag(status, WS_STATUS_INTERNAL); }
 
-    // ---- cluster values
+    // ---- cluster values (a one-element cluster reads its weight back from the input)
     for (int r = t; r < c; r += NT) {
-        int a = s.V[r], b = s.V[r + 1];
-        T xs = KO::from_key(s.keys[a]);
-        s.u.out.val[r] = ValueOut<T>::value(X(b) - X(a), a, b, xs, sc, fp64 != 0);
-        s.u.out.mark[a] = 1;
+        const int a = s.r1.ids.V[r], b = s.r1.ids.V[r + 1];
+        const T xs = (b - a == 1) ? values[a0 + s.idx[a]] : (T)0;
+        s.r2.val[r] = ValueOut<T>::value(X(b) - X(a), a, b, xs, sc, fp64 != 0);
+        atomicOr(&s.r1.ids.mark[a >> 5], 1u << (a & 31));
     }
     __syncthreads();
 
     // ---- cluster id of every sorted position, then scatter to the original order
-    int cntm = 0;
-    for (int i = 0; i < M; ++i) { int p = t * M + i; if (p < n) cntm += s.u.out.mark[p]; }
+    const uint32_t mymarks = (s.r1.ids.mark[(t * M) >> 5] >> ((t * M) & 31)) & (uint32_t)((1ull << M) - 1ull);
     int tot;
-    int run = ws_block_excl_scan<NT, int>(cntm, s.wsum_i, &tot);
+    int run = ws_block_excl_scan<NT, int>(__popc(mymarks), s.wsum_i, &tot);
     for (int i = 0; i < M; ++i) {
         int p = t * M + i;
         if (p < n) {
-            run += s.u.out.mark[p];
+            run += (mymarks >> i) & 1u;
             int r = run - 1;
             int64_t o = a0 + s.idx[p];
-            out[o] = s.u.out.val[r];
+            out[o] = s.r2.val[r];
             if (ids) ids[o] = r;
         }
     }
