@@ -353,10 +353,10 @@ static __device__ __noinline__ bool ws_convex_binade_exact(int64_t A, int64_t B,
 // segment).  When range * n^2 <= 2^62 (every FP32 binade tile), Delta =
 // B n1 - A n2 is exact in 64 bits and only the right-hand side mu (c-a) n1 n2
 // is rounded, so the FP32 filter's error is relative to |Delta| + rhs rather
-// than to the cancelling terms B n1 and A n2: Delta is converted once (2^-24),
-// mu, the product and the multiply add <= 4 roundings to rhs (2^-24 each) and
+// than to the cancelling terms B n1 and A n2: converting Delta > 0 costs <= 3
+// roundings (2^-24 each), mu, the product and the multiply add <= 4 to rhs,
 // the subtraction one more, < 3.1e-7 (Delta + rhs) in all; the 6e-7 margin
-// covers that twice.  Otherwise (FP64 keys spread over a wide range) the
+// covers that.  Otherwise (FP64 keys spread over a wide range) the
 // filter runs on the rounded terms as in TilePts.  Near-ties fall through to
 // the exact integer test.
 template <int M>
@@ -390,7 +390,7 @@ struct TilePtsDev {
             if (D <= 0) return false;
             if (modd == 0) return true;
             if (fast) {
-                const float Df = (float)D;
+                const float Df = ws_u64_to_float((uint64_t)D);
                 const float rhs = muq * ((float)(c - a) * (float)((b - a) * (c - b)));
                 const float diff = Df - rhs;
                 const float err = 6.0e-7f * (Df + rhs);
@@ -401,11 +401,12 @@ struct TilePtsDev {
             if (r >= 0) return r != 0;
         } else if (fast) {
             const float n1 = (float)(b - a), n2 = (float)(c - b);
-            const float fB = (float)B * n1;
-            const float fA = (float)A * n2;
+            // A, B >= 0 (deviations from the tile's first point, sorted order)
+            const float fB = ws_u64_to_float((uint64_t)B) * n1;
+            const float fA = ws_u64_to_float((uint64_t)A) * n2;
             const float rhs = muq * (float)(c - a) * n1 * n2;
             const float diff = (fB - fA) - rhs;
-            const float err = 4.0e-7f * (fabsf(fB) + fabsf(fA) + rhs);
+            const float err = 5.0e-7f * (fabsf(fB) + fabsf(fA) + rhs);
             if (diff > err) return true;
             if (diff < -err) return false;
         }

@@ -255,13 +255,19 @@ __device__ __forceinline__ bool ws_convex(i128 Xa, i128 Xb, i128 Xc, int64_t a, 
 // ---------------------------------------------------------------------------
 // v * 2^-neg_exp, rounded to float (high and low 64-bit halves converted
 // separately, so all significant bits take part in the rounding).
+// Positive 64-bit integer to float from its two 32-bit halves (no 64-bit
+// conversion instruction, which GB300 runs at its FP64 rate): the halves
+// round once each and the fused add once more, <= 3 * 2^-24 relative.
+__device__ __forceinline__ float ws_u64_to_float(uint64_t v) {
+    return fmaf((float)(uint32_t)(v >> 32), 4294967296.0f, (float)(uint32_t)v);
+}
 __device__ __forceinline__ float ws_i128_to_float_scaled(i128 v, int neg_exp) {
-    // keep the top 62 significant bits (exact shift), then one rounding to float
+    // keep the top 62 significant bits (exact shift), then convert (<= 3 roundings)
     u128 mag = v < 0 ? (u128)(-v) : (u128)v;
     int sh = ws_bitlen128(mag) - 62;
     if (sh < 0) sh = 0;
-    long long t = (long long)(v >> sh);
-    return ldexpf(__ll2float_rn(t), sh - neg_exp);
+    const float f = ws_u64_to_float((uint64_t)(mag >> sh));
+    return ldexpf(v < 0 ? -f : f, sh - neg_exp);
 }
 __device__ __forceinline__ double ws_i128_to_double(i128 v) {
     long long hi = (long long)(v >> 64);
