@@ -215,7 +215,8 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->npieces, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->tile_piece, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->rt, sizeof(SegRuntime) * p->n_lseg))) return st;
-    if ((st = plan_alloc(p, &p->table, (f64 ? sizeof(CEntry<double>) : sizeof(CEntry<float>)) * slots))) return st;
+    // (+4 entries: the lookup reads whole 32-byte sectors of the table)
+    if ((st = plan_alloc(p, &p->table, (f64 ? sizeof(CEntry<double>) : sizeof(CEntry<float>)) * (slots + 4)))) return st;
     if ((st = plan_alloc(p, (void**)&p->dir, sizeof(DirEntry) * (size_t)dir_pos))) return st;
     if ((st = plan_alloc(p, &p->bsum, vsize * slots))) return st;
     if ((st = plan_alloc(p, (void**)&p->bcnt, sizeof(int32_t) * slots))) return st;

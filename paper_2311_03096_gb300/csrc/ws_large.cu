@@ -592,34 +592,73 @@ __global__ void __launch_bounds__(256) k_big_gaps(const BigGap* gaps, const uint
 // ---------------------------------------------------------------------------
 // 6. lookup: every weight, in the caller's order, finds its cluster by value
 // ---------------------------------------------------------------------------
-// Last cluster in [lo, hi) whose start key is <= k, else lo - 1; starts from
-// the guess g (interpolated on the 32-bit key prefix) and steps, bisecting if
-// the guess is far off.
+// The cluster table is read a whole 32-byte sector at a time (E entries): the
+// sector holding the interpolated guess almost always contains the answer,
+// so a weight costs about one random sector instead of one per probed entry.
 template <typename T>
-__device__ __forceinline__ int ws_find_cluster(const CEntry<T>* tab, int lo, int hi, int g, typename KeyOf<T>::K k,
-                                               typename KeyOf<T>::K kg) {
-    int steps = 0;
-    if (kg <= k) {
-        while (g + 1 < hi && tab[g + 1].key <= k && ++steps < 8) ++g;
-    } else {
-        while (g > lo && tab[g].key > k && ++steps < 8) --g;
-        if (tab[g].key > k) g = lo - 1;
+struct TabSector {
+    static constexpr int E = 32 / (int)sizeof(CEntry<T>);
+    CEntry<T> e[E];
+    __device__ __forceinline__ void load(const CEntry<T>* table, int64_t sb) {
+        const uint4* p = reinterpret_cast<const uint4*>(table + sb);
+        uint4 v[2];
+        v[0] = __ldg(p);
+        v[1] = __ldg(p + 1);
+        const CEntry<T>* q = reinterpret_cast<const CEntry<T>*>(v);
+#pragma unroll
+        for (int i = 0; i < E; ++i) e[i] = q[i];
     }
-    if (steps >= 8) {
-        int l = lo, h = hi;
-        while (l < h) {
-            const int mid = (l + h) >> 1;
-            if (tab[mid].key <= k) l = mid + 1; else h = mid;
+};
+
+// Last cluster j in [jlo, jhi] (segment-local, keys ascending, key[jlo] <= k)
+// whose start key is <= k, starting at the sector that holds local index j0
+// and walking sector by sector (at most four, then bisection).
+template <typename T>
+__device__ __forceinline__ int ws_find_cluster(const CEntry<T>* table, int64_t tp, int jlo, int jhi, int j0,
+                                               typename KeyOf<T>::K k, CEntry<T>& out) {
+    constexpr int E = TabSector<T>::E;
+    int j = min(max(j0, jlo), jhi);
+    int best = -1, dir = 0;
+    for (int it = 0; it < 4; ++it) {
+        const int64_t sb = (tp + j) & ~(int64_t)(E - 1);
+        const int s0 = (int)(sb - tp);
+        TabSector<T> S;
+        S.load(table, sb);
+        int last_le = -1, top = -1;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int li = s0 + i;
+            if (li < jlo || li > jhi) continue;
+            top = li;
+            if (S.e[i].key <= k) { last_le = li; out = S.e[i]; }
         }
-        g = l - 1;
+        if (last_le < 0) {              // every entry here is above k
+            if (dir > 0) return best;   // ... and the previous sector's last one was not: out holds it
+            if (s0 - 1 < jlo) break;    // (cannot happen: key[jlo] <= k)
+            dir = -1;                   // the answer lies further left
+            j = s0 - 1;
+            continue;
+        }
+        best = last_le;
+        // an entry above k follows inside this sector, the range ends here, or
+        // the sector to the right was all above k: the answer is here
+        if (last_le < top || last_le == jhi || dir < 0) return best;
+        dir = 1;
+        j = s0 + E;
     }
-    return g;
+    int l = jlo, h = jhi + 1;   // bisection fallback
+    while (l < h) {
+        const int mid = (l + h) >> 1;
+        if (table[tp + mid].key <= k) l = mid + 1; else h = mid;
+    }
+    out = table[tp + l - 1];
+    return l - 1;
 }
 
 // Every weight, in the caller's order, finds its cluster by value: bucket ->
-// directory (L2-resident) -> interpolated probe of the cluster table.  Each
-// thread carries LK elements through every stage so that their independent
-// random loads overlap.
+// directory (L2-resident) -> interpolated guess -> the table sector holding
+// it.  Each thread carries LK elements through every stage so that their
+// independent random loads overlap.
 template <typename T>
 __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, const TileDesc* __restrict__ tiles,
                                                 const LargeSeg* __restrict__ lsegs, const SegRuntime* __restrict__ rt,
@@ -633,7 +672,7 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
     const SegRuntime R = rt[td.lseg];
     const int nb = 1 << R.dir_log2;
     const DirEntry* D = dir + ls.dir_pos;
-    const CEntry<T>* tab = table + R.table_pos;
+    const int64_t tp = R.table_pos;
     const int c = (int)R.n_clusters;
     const uint64_t pol = ws_policy_evict_last();
     for (int i0 = threadIdx.x; i0 < td.len; i0 += 256 * LK) {
@@ -662,7 +701,7 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
             lo[u] = min(max(e0[u].idx, 0), c);
             hi[u] = min(max(e1[u].idx, lo[u]), c);
             if (lo[u] == hi[u] || k32 < e0[u].key32) {
-                g[u] = -1;   // precedes every start in the bucket: cluster lo - 1
+                g[u] = lo[u] - 1;   // precedes every start in the bucket: cluster lo - 1
             } else {
                 const uint32_t span = e1[u].key32 - e0[u].key32;
                 int gg = lo[u];
@@ -674,20 +713,14 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
                 g[u] = gg;
             }
         }
-        CEntry<T> cg[LK];
-#pragma unroll
-        for (int u = 0; u < LK; ++u) cg[u] = tab[g[u] >= 0 ? g[u] : max(lo[u] - 1, 0)];
 #pragma unroll
         for (int u = 0; u < LK; ++u) {
-            int r;
-            CEntry<T> ce = cg[u];
-            if (g[u] < 0) {
-                r = lo[u] - 1;
-            } else {
-                r = ws_find_cluster<T>(tab, lo[u], hi[u], g[u], k[u], ce.key);
-                if (r != g[u] && r >= 0) ce = tab[r];
-            }
-            if (r < 0 || r >= c) { ws_flag(status, WS_STATUS_INTERNAL); r = 0; ce = tab[0]; }
+            CEntry<T> ce;
+            const int jlo = max(lo[u] - 1, 0), jhi = max(hi[u] - 1, jlo);
+            int r = jlo;
+            if (jhi == jlo) ce = table[tp + jlo];   // one candidate: no search
+            else r = ws_find_cluster<T>(table, tp, jlo, jhi, g[u], k[u], ce);
+            if (r < 0 || r >= c) { ws_flag(status, WS_STATUS_INTERNAL); r = 0; ce = table[tp]; }
             if (in[u]) {
                 const int i = i0 + u * 256;
                 __stcs(out + td.vpos + i, ce.val);
