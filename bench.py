@@ -36,7 +36,7 @@ LAMBDAS = (1e-2, 1.0, 1e2)
 WORKLOAD = "single vector d=2^26 FP32 N(0,1) + 10% exact duplicates, lambda cycling {1e-2, 1, 1e2}"
 
 # Algorithmic HBM bytes per element for each kernel kind of the device-wide
-# path (FP32 storage; documented with the roofline in the design doc).
+# path (FP32 storage): what a launch must read and write at the least.
 ALGO_BYTES_PER_ELEM_F32 = {
     "onesweep": 8,    # read key (pass 0: the value) + write key
     "hist": 4,        # read the value

@@ -48,6 +48,9 @@ def _load():
             lib.ws_oracle_prox.argtypes = [_f64p, ctypes.c_int64, ctypes.c_double, _f64p, _i32p, _i64p,
                                            _f64p, _i64p]
             lib.ws_oracle_prox.restype = ctypes.c_int
+            lib.ws_oracle_prox_l1.argtypes = [_f64p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, _f64p, _i32p, _i64p]
+            lib.ws_oracle_prox_l1.restype = ctypes.c_int
             lib.ws_oracle_prox_batched.argtypes = [_f64p, _i64p, ctypes.c_int64, _f64p, _f64p, _i32p, _i64p]
             lib.ws_oracle_prox_batched.restype = ctypes.c_int
             lib.ws_oracle_backward.argtypes = [_f64p, _i32p, _i64p, ctypes.c_int64, ctypes.c_int64, _f64p]
@@ -97,6 +100,18 @@ def prox(w, lam: float, *, return_perm: bool = False):
     if return_perm:
         return out, ids, int(nc.value), perm, xs
     return out, ids, int(nc.value)
+
+
+def prox_l1(w, alpha: float, beta: float, rho: float = 0.0, v_scale: float = 1.0):
+    """Weight sharing + l1 with rewinding (Alg. 2) in FP64.  Returns (out, ids, n_clusters)."""
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    d = w.shape[0]
+    out = np.empty(d, np.float64)
+    ids = np.empty(d, np.int32)
+    nc = np.zeros(1, np.int64)
+    _check(_load().ws_oracle_prox_l1(_p(w, _f64p), d, float(alpha), float(beta), float(rho), float(v_scale),
+                                     _p(out, _f64p), _p(ids, _i32p), _p(nc, _i64p)))
+    return out, ids, int(nc[0])
 
 
 def prox_batched(values, offsets, lambdas):

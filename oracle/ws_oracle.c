@@ -30,7 +30,7 @@
  *      out[perm[k]] = value(block of k), ids[perm[k]] = r  (Alg. 2:
  *      repeat_interleave then scatter by sort_indices).
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *   - ties in the merge pool on ">=" (text of Sec. 4.1), so clusters are
  *     maximal runs of equal prox values;
  *   - the sort key is the IEEE-754 total order of binary64 (so -0 < +0), ties
@@ -197,6 +197,94 @@ int ws_oracle_prox(const double* w, int64_t d, double lambda, double* out, int32
         for (int64_t j = 0; j < d; ++j) x_sorted[j] = w[perm[j]];
     if (n_clusters) *n_clusters = top;
     free(perm); free(y); free(bsum); free(bcnt);
+    return 0;
+}
+
+/*
+ * ws_oracle_prox_l1: the proximal step with weight sharing, l1 and rewinding
+ * (Rewinding section, Alg. 2), following the algorithm's steps:
+ *   1. x, perm = sort(w) (stable);
+ *   2. v_k = alpha (d + 1 - 2k)/(d - 1), k = 1..d (the velocities, -alpha grad R);
+ *      every particle has mass 1;
+ *   3. collisions: particles whose destinations x + v cross merge into one
+ *      cluster carrying the sums of x and of v (momentum is conserved, so the
+ *      cluster moves with the mean velocity); computed as pool adjacent
+ *      violators on y = x + v, pooling on >= as in ws_oracle_prox, with the
+ *      cluster's x-sum and v-sum carried alongside the y-sum;
+ *   4. per cluster with mean position x_C and mean velocity v_C:
+ *        zero  = |x_C + v_C| < beta
+ *        v_C  -= beta sign(x_C + v_C)
+ *        x_C = v_C = 0 where zero
+ *        x_C  += v_scale (1 - rho) v_C
+ *      (v_scale = 1 is Alg. 2; the experiments' variant multiplies the
+ *      remaining displacement by the learning rate instead of scaling alpha
+ *      and beta by it, which is v_scale = learning rate);
+ *   5. repeat per cluster and scatter back by perm.
+ * ids as in ws_oracle_prox (the clusters of the weight-sharing step).
+ * Returns 0, 1 (invalid: beta < 0, rho outside [0, 1], v_scale < 0 or any of
+ * them non-finite), 2 (non-finite input) or 4 (OOM).
+ */
+int ws_oracle_prox_l1(const double* w, int64_t d, double alpha, double beta, double rho, double v_scale,
+                      double* out, int32_t* ids, int64_t* n_clusters) {
+    if (d < 0 || !(alpha >= 0.0) || !isfinite(alpha) || !(beta >= 0.0) || !isfinite(beta) || !(rho >= 0.0) ||
+        !(rho <= 1.0) || !(v_scale >= 0.0) || !isfinite(v_scale))
+        return 1;
+    if (d == 0) {
+        if (n_clusters) *n_clusters = 0;
+        return 0;
+    }
+    for (int64_t i = 0; i < d; ++i)
+        if (!isfinite(w[i])) return 2;
+    int64_t* perm = (int64_t*)malloc((size_t)d * sizeof(int64_t));
+    csum* ysum = (csum*)malloc((size_t)d * sizeof(csum));
+    csum* xsum = (csum*)malloc((size_t)d * sizeof(csum));
+    csum* vsum = (csum*)malloc((size_t)d * sizeof(csum));
+    int64_t* bcnt = (int64_t*)malloc((size_t)d * sizeof(int64_t));
+    if (!perm || !ysum || !xsum || !vsum || !bcnt) {
+        free(perm); free(ysum); free(xsum); free(vsum); free(bcnt);
+        return 4;
+    }
+    int rc = sort_perm(w, d, perm);
+    if (rc) {
+        free(perm); free(ysum); free(xsum); free(vsum); free(bcnt);
+        return rc;
+    }
+    int64_t top = 0;
+    for (int64_t k = 1; k <= d; ++k) {
+        const double xk = w[perm[k - 1]];
+        const double vk = d > 1 ? alpha * (double)(d + 1 - 2 * k) / (double)(d - 1) : 0.0;
+        ysum[top].s = xk + vk; ysum[top].c = 0.0;
+        xsum[top].s = xk; xsum[top].c = 0.0;
+        vsum[top].s = vk; vsum[top].c = 0.0;
+        bcnt[top] = 1;
+        ++top;
+        while (top >= 2) {
+            double mean_left = csum_value(&ysum[top - 2]) / (double)bcnt[top - 2];
+            double mean_right = csum_value(&ysum[top - 1]) / (double)bcnt[top - 1];
+            if (!(mean_left >= mean_right)) break;
+            csum_merge(&ysum[top - 2], &ysum[top - 1]);
+            csum_merge(&xsum[top - 2], &xsum[top - 1]);
+            csum_merge(&vsum[top - 2], &vsum[top - 1]);
+            bcnt[top - 2] += bcnt[top - 1];
+            --top;
+        }
+    }
+    int64_t k = 0;
+    for (int64_t r = 0; r < top; ++r) {
+        double x = csum_value(&xsum[r]) / (double)bcnt[r];
+        double v = csum_value(&vsum[r]) / (double)bcnt[r];
+        const double s = x + v;
+        const int zero = fabs(s) < beta;
+        v -= beta * (double)((s > 0.0) - (s < 0.0));
+        if (zero) { x = 0.0; v = 0.0; }
+        x += v_scale * (1.0 - rho) * v;
+        for (int64_t j = 0; j < bcnt[r]; ++j, ++k) {
+            out[perm[k]] = x;
+            if (ids) ids[perm[k]] = (int32_t)r;
+        }
+    }
+    if (n_clusters) *n_clusters = top;
+    free(perm); free(ysum); free(xsum); free(vsum); free(bcnt);
     return 0;
 }
 

@@ -318,3 +318,73 @@ def test_error_paths():
     assert nc == 0
     out, ids, nc = oracle.prox(np.array([3.5]), 10.0)
     assert out.tolist() == [3.5] and ids.tolist() == [0] and nc == 1
+
+
+# -- weight sharing + l1 with rewinding (Rewinding section, Alg. 2) ----------
+
+def test_l1_rewind_reduces_to_prox_when_beta_zero():
+    rng = np.random.default_rng(31)
+    for d in (1, 2, 7, 500):
+        w = rng.standard_normal(d)
+        for lam in (0.0, 0.05, 1.0):
+            ref, rid, rn = oracle.prox(w, lam)
+            out, ids, nc = oracle.prox_l1(w, lam, 0.0, 0.0)
+            assert nc == rn and np.array_equal(ids, rid)
+            np.testing.assert_allclose(out, ref, rtol=0, atol=1e-13 * (1 + np.abs(w).max() + lam))
+
+
+def test_l1_rewind_without_sharing_is_eq_rewinding_l1():
+    # alpha = 0: every cluster is one value, and Alg. 2 reduces to the closed form
+    # (w - (1 - rho) beta sign(w)) [|w| > beta] of Eq. rewinding_l1 (no |w| == beta ties here)
+    rng = np.random.default_rng(32)
+    w = rng.standard_normal(2000)
+    for beta in (0.0, 0.3, 1.5):
+        for rho in (0.0, 0.25, 1.0):
+            out, _, _ = oracle.prox_l1(w, 0.0, beta, rho)
+            expect = np.where(np.abs(w) > beta, w - (1 - rho) * beta * np.sign(w), 0.0)
+            np.testing.assert_allclose(out, expect, rtol=0, atol=1e-15)
+
+
+def test_l1_rewind_rho0_is_soft_threshold_of_prox():
+    # Prop. D.6: prox of alpha R + beta l1 = soft-thresholding of prox of alpha R
+    rng = np.random.default_rng(33)
+    for d in (3, 64, 3000):
+        w = rng.standard_normal(d)
+        for lam in (0.01, 0.4, 3.0):
+            p, pid, _ = oracle.prox(w, lam)
+            for beta in (0.05, 0.5):
+                out, ids, _ = oracle.prox_l1(w, lam, beta, 0.0)
+                assert np.array_equal(ids, pid)
+                st = np.sign(p) * np.maximum(np.abs(p) - beta, 0.0)
+                np.testing.assert_allclose(out, st, rtol=0, atol=1e-12 * (1 + np.abs(w).max() + lam))
+
+
+def test_l1_rewind_rho1_keeps_cluster_means():
+    # rho = 1 removes the whole remaining displacement: surviving clusters sit at
+    # the mean of their weights, the others at 0
+    rng = np.random.default_rng(34)
+    w = rng.standard_normal(1500)
+    lam, beta = 0.7, 0.2
+    p, pid, nc = oracle.prox(w, lam)
+    out, ids, _ = oracle.prox_l1(w, lam, beta, 1.0)
+    mean = np.bincount(ids, weights=w, minlength=nc) / np.bincount(ids, minlength=nc)
+    keep = np.abs(p) >= beta
+    np.testing.assert_allclose(out[keep], mean[ids][keep], rtol=0, atol=1e-12)
+    assert np.all(out[~keep] == 0.0)
+
+
+def test_l1_rewind_is_affine_in_the_displacement_scale():
+    rng = np.random.default_rng(35)
+    w = rng.standard_normal(800)
+    lam, beta, rho = 0.3, 0.1, 0.4
+    a = oracle.prox_l1(w, lam, beta, rho, 0.0)[0]
+    b = oracle.prox_l1(w, lam, beta, rho, 1.0)[0]
+    h = oracle.prox_l1(w, lam, beta, rho, 0.5)[0]
+    np.testing.assert_allclose(h, 0.5 * (a + b), rtol=0, atol=1e-13)
+
+
+def test_l1_rewind_rejects_bad_arguments():
+    w = np.zeros(4)
+    for args in ((-1.0, 0.0), (0.1, -0.5), (0.1, 1.5), (0.1, float("nan"))):
+        with pytest.raises(oracle.OracleError):
+            oracle.prox_l1(w, 0.1, args[0], args[1])
