@@ -100,6 +100,34 @@ ws_status ws_prox(ws_ctx* ctx, const void* w, int64_t d, double lambda, void* ou
                   int32_t* cluster_ids, int64_t* n_clusters, ws_dtype dtype, ws_prec prec,
                   void* stream);
 
+/* Weight sharing + l1 with rewinding: the proximal step of Alg. 2 (Rewinding
+ * section).  The clusters are those of ws_prox / ws_prox_batched; a cluster
+ * with mean weight x and mean shift v (the mean of lambda (d+1-2k)/(d-1) over
+ * its sorted positions k) ends at
+ *     0                                        if |x + v| < beta,
+ *     x + v_scale (1 - rho) (v - beta sign(x + v))   otherwise.
+ * rho = 0 and v_scale = 1 give prox of lambda R + beta l1, i.e. the soft
+ * threshold of prox_{lambda R} (Prop. D.6); rho = 1 leaves surviving
+ * clusters at their mean weight; v_scale = the learning rate is the
+ * experiments' variant that scales the remaining displacement instead of
+ * lambda and beta.  Computed inside the cluster-value step: no extra pass.
+ * beta >= 0, 0 <= rho <= 1, v_scale >= 0, all finite, else WS_ERR_INVALID
+ * (nothing is enqueued); epi must not be NULL.  Other arguments, layouts,
+ * ownership and errors as for ws_prox_batched / ws_prox.  cluster_ids are the
+ * weight-sharing clusters (zeroed clusters keep their own ids). */
+typedef struct ws_l1_rewind {
+    double beta;     /* l1 coefficient */
+    double rho;      /* rewinding, 0 (none) .. 1 (full) */
+    double v_scale;  /* scale of the remaining displacement (1 in Alg. 2) */
+} ws_l1_rewind;
+
+ws_status ws_prox_batched_l1(ws_plan* plan, const void* values, const double* lambdas,
+                             const ws_l1_rewind* epi, void* out, int32_t* cluster_ids,
+                             int64_t* n_clusters, ws_prec prec, void* stream);
+ws_status ws_prox_l1(ws_ctx* ctx, const void* w, int64_t d, double lambda, const ws_l1_rewind* epi,
+                     void* out, int32_t* cluster_ids, int64_t* n_clusters, ws_dtype dtype,
+                     ws_prec prec, void* stream);
+
 /* Backward of the forward with the partition held fixed (the Jacobian of the
  * cluster means): grad_in[i] = mean of grad_out over the cluster of i, where
  * clusters are given by (segment, cluster_ids[i]) as written by the forward on

@@ -234,14 +234,14 @@ ws_status map_cuda(cudaError_t e) {
 
 template <typename T>
 ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, void* out, int32_t* ids,
-                      int64_t* n_clusters, ws_prec prec, cudaStream_t st) {
+                      int64_t* n_clusters, ws_prec prec, const WsEpi& ep, cudaStream_t st) {
     const int fp64 = prec == WS_PREC_FP64 ? 1 : 0;
     cudaError_t e = ws_launch_small<T>((const T*)values, p->d_offsets, p->d_small, p->n_small, lambdas, (T*)out, ids,
-                                       n_clusters, fp64, p->ctx->status, st, &p->ctx->prof);
+                                       n_clusters, fp64, ep, p->ctx->status, st, &p->ctx->prof);
     if (e) return map_cuda(e);
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);
-        e = ws_large_prox<T>(W, (const T*)values, lambdas, (T*)out, ids, n_clusters, fp64, p->ctx->status,
+        e = ws_large_prox<T>(W, (const T*)values, lambdas, (T*)out, ids, n_clusters, fp64, ep, p->ctx->status,
                              p->ctx->spin_limit, p->n_levels, st);
         if (e) return map_cuda(e);
     }
@@ -353,30 +353,73 @@ void ws_plan_destroy(ws_plan* plan) {
     delete plan;
 }
 
-ws_status ws_prox_batched(ws_plan* plan, const void* values, const double* lambdas, void* out, int32_t* cluster_ids,
-                          int64_t* n_clusters, ws_prec prec, void* stream) {
+// Epilogue constants (all-off when epi is null); WS_ERR_INVALID on bad values.
+static ws_status make_epi(const ws_l1_rewind* epi, WsEpi* ep) {
+    ep->on = 0; ep->beta = 0.0; ep->gamma = 1.0; ep->beta_f = 0.0f; ep->gamma_f = 1.0f;
+    if (!epi) return WS_OK;
+    const double big = 1.7976931348623157e308;
+    if (!(epi->beta >= 0.0) || !(epi->beta <= big) || !(epi->rho >= 0.0) || !(epi->rho <= 1.0) ||
+        !(epi->v_scale >= 0.0) || !(epi->v_scale <= big))
+        return WS_ERR_INVALID;
+    ep->on = 1;
+    ep->beta = epi->beta;
+    ep->gamma = epi->v_scale * (1.0 - epi->rho);
+    ep->beta_f = (float)ep->beta;
+    ep->gamma_f = (float)ep->gamma;
+    return WS_OK;
+}
+
+static ws_status batched_impl(ws_plan* plan, const void* values, const double* lambdas, const ws_l1_rewind* epi, void* out,
+                       int32_t* cluster_ids, int64_t* n_clusters, ws_prec prec, void* stream) {
     if (!plan || (prec != WS_PREC_FP32_COMP && prec != WS_PREC_FP64)) return WS_ERR_INVALID;
     if (plan->n > 0 && (!values || !out)) return WS_ERR_INVALID;
     if (plan->n_seg > 0 && !lambdas) return WS_ERR_INVALID;
+    WsEpi ep;
+    if (make_epi(epi, &ep) != WS_OK) return WS_ERR_INVALID;
     if (plan->n_seg == 0) return WS_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    return plan->dtype == WS_F64 ? run_forward<double>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, st)
-                                 : run_forward<float>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, st);
+    return plan->dtype == WS_F64
+               ? run_forward<double>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, ep, st)
+               : run_forward<float>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, ep, st);
 }
 
-ws_status ws_prox(ws_ctx* ctx, const void* w, int64_t d, double lambda, void* out, int32_t* cluster_ids,
-                  int64_t* n_clusters, ws_dtype dtype, ws_prec prec, void* stream) {
+static ws_status single_impl(ws_ctx* ctx, const void* w, int64_t d, double lambda, const ws_l1_rewind* epi, void* out,
+                      int32_t* cluster_ids, int64_t* n_clusters, ws_dtype dtype, ws_prec prec, void* stream) {
     if (!ctx || d < 0 || !(lambda >= 0.0) || !(lambda <= 1.7976931348623157e308)) return WS_ERR_INVALID;
     if (dtype != WS_F32 && dtype != WS_F64) return WS_ERR_INVALID;
     if (d > 0 && (!w || !out)) return WS_ERR_INVALID;
     if (d >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    WsEpi ep;
+    if (make_epi(epi, &ep) != WS_OK) return WS_ERR_INVALID;
     ws_status st;
     ws_plan* p = cached_plan(ctx, d, dtype, &st);
     if (!p) return st;
     cudaStream_t s = (cudaStream_t)stream;
     WS_LAUNCH(&ctx->prof, WSK_MISC, s, (k_set_lambda<<<1, 1, 0, s>>>(p->d_lambda1, lambda)));
     if (cudaGetLastError() != cudaSuccess) return WS_ERR_CUDA;
-    return ws_prox_batched(p, w, p->d_lambda1, out, cluster_ids, n_clusters, prec, stream);
+    return batched_impl(p, w, p->d_lambda1, epi, out, cluster_ids, n_clusters, prec, stream);
+}
+
+ws_status ws_prox_batched(ws_plan* plan, const void* values, const double* lambdas, void* out, int32_t* cluster_ids,
+                          int64_t* n_clusters, ws_prec prec, void* stream) {
+    return batched_impl(plan, values, lambdas, nullptr, out, cluster_ids, n_clusters, prec, stream);
+}
+
+ws_status ws_prox_batched_l1(ws_plan* plan, const void* values, const double* lambdas, const ws_l1_rewind* epi,
+                             void* out, int32_t* cluster_ids, int64_t* n_clusters, ws_prec prec, void* stream) {
+    if (!epi) return WS_ERR_INVALID;
+    return batched_impl(plan, values, lambdas, epi, out, cluster_ids, n_clusters, prec, stream);
+}
+
+ws_status ws_prox(ws_ctx* ctx, const void* w, int64_t d, double lambda, void* out, int32_t* cluster_ids,
+                  int64_t* n_clusters, ws_dtype dtype, ws_prec prec, void* stream) {
+    return single_impl(ctx, w, d, lambda, nullptr, out, cluster_ids, n_clusters, dtype, prec, stream);
+}
+
+ws_status ws_prox_l1(ws_ctx* ctx, const void* w, int64_t d, double lambda, const ws_l1_rewind* epi, void* out,
+                     int32_t* cluster_ids, int64_t* n_clusters, ws_dtype dtype, ws_prec prec, void* stream) {
+    if (!epi) return WS_ERR_INVALID;
+    return single_impl(ctx, w, d, lambda, epi, out, cluster_ids, n_clusters, dtype, prec, stream);
 }
 
 ws_status ws_prox_backward_batched(ws_plan* plan, const void* grad_out, const int32_t* cluster_ids, void* grad_in,

@@ -275,32 +275,51 @@ __device__ __forceinline__ double ws_i128_to_double(i128 v) {
     return fma(__ll2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo));
 }
 
+// Weight sharing + l1 with rewinding (Rewinding section, Alg. 2): a cluster
+// with mean position x and mean velocity v (its shift) ends at
+//   0                                  if |x + v| < beta,
+//   x + gamma (v - beta sign(x + v))   otherwise, gamma = v_scale (1 - rho);
+// with the epilogue off it ends at x + v (the prox of lambda R alone).
+struct WsEpi {
+    double beta, gamma;
+    float beta_f, gamma_f;
+    int on;
+};
+
+template <typename V>
+__device__ __forceinline__ V ws_epilogue(V x, V v, V beta, V gamma, bool on) {
+    const V s = x + v;
+    if (!on) return s;
+    if ((s < (V)0 ? -s : s) < beta) return (V)0;
+    return x + gamma * (v - (s > (V)0 ? beta : -beta));
+}
+
 template <typename T> struct ValueOut;
 template <> struct ValueOut<float> {
     __device__ __forceinline__ static float value(i128 SX, int64_t a, int64_t b, float xsingle, const SegConst& sc,
-                                                  bool fp64) {
+                                                  bool fp64, const WsEpi& ep) {
         int64_t n = b - a;
         int64_t t = sc.d - a - b;
         if (fp64) {
             double mean = (n == 1) ? (double)xsingle : ldexp(ws_i128_to_double(SX) / (double)n, -sc.L);
-            return (float)(mean + sc.mu_d * (double)t);
+            return (float)ws_epilogue<double>(mean, sc.mu_d * (double)t, ep.beta, ep.gamma, ep.on != 0);
         }
         float mean = (n == 1) ? xsingle : ldexpf(ws_i128_to_float_scaled(SX, 0) / (float)n, -sc.L);
-        return mean + sc.mu_f * (float)t;
+        return ws_epilogue<float>(mean, sc.mu_f * (float)t, ep.beta_f, ep.gamma_f, ep.on != 0);
     }
 };
 template <> struct ValueOut<double> {
     __device__ __forceinline__ static double value(i128 SX, int64_t a, int64_t b, double xsingle,
-                                                   const SegConst& sc, bool fp64) {
+                                                   const SegConst& sc, bool fp64, const WsEpi& ep) {
         int64_t n = b - a;
         int64_t t = sc.d - a - b;
         if (!fp64) {
             // FP32 arithmetic on the exact sum, widened to the output type
             float mean = (n == 1) ? (float)xsingle : ldexpf(ws_i128_to_float_scaled(SX, 0) / (float)n, -sc.L);
-            return (double)(mean + sc.mu_f * (float)t);
+            return (double)ws_epilogue<float>(mean, sc.mu_f * (float)t, ep.beta_f, ep.gamma_f, ep.on != 0);
         }
         double mean = (n == 1) ? xsingle : ldexp(ws_i128_to_double(SX) / (double)n, -sc.L);
-        return mean + sc.mu_d * (double)t;
+        return ws_epilogue<double>(mean, sc.mu_d * (double)t, ep.beta, ep.gamma, ep.on != 0);
     }
 };
 

@@ -103,7 +103,7 @@ struct SegRuntime {
 template <typename T>
 cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
                             const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
-                            uint32_t* status, cudaStream_t st, WsProf* prof);
+                            const WsEpi& ep, uint32_t* status, cudaStream_t st, WsProf* prof);
 template <typename T>
 cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64_t* offsets, const int32_t* seg_list,
                                      int n_list, T* gin, uint32_t* status, cudaStream_t st, WsProf* prof);
@@ -147,8 +147,8 @@ cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* stat
                           cudaStream_t st, typename KeyOf<T>::K** sorted);
 template <typename T>
 cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* lambdas, T* out, int32_t* ids,
-                          int64_t* n_clusters, int fp64, uint32_t* status, uint64_t spin_limit, int n_levels,
-                          cudaStream_t st);
+                          int64_t* n_clusters, int fp64, const WsEpi& ep, uint32_t* status, uint64_t spin_limit,
+                          int n_levels, cudaStream_t st);
 template <typename T>
 cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* ids, T* gin, uint32_t* status,
                               cudaStream_t st);

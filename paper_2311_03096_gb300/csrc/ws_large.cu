@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
                                                const int32_t* __restrict__ npieces,
                                                const int32_t* __restrict__ tile_piece, CEntry<T>* table,
                                                DirEntry* dir, BigGap* gaps, uint32_t* ngaps, int64_t gap_cap,
-                                               int fp64, uint32_t* status) {
+                                               int fp64, const WsEpi ep, uint32_t* status) {
     typedef KeyOf<T> KO;
     const int tile = blockIdx.x;
     const int tp = tile_piece[tile];
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htil
         T xs = KO::from_key(k);
         CEntry<T> ce;
         ce.key = k;
-        ce.val = ValueOut<T>::value(Xb - Xa, a, b, xs, sc, fp64 != 0);
+        ce.val = ValueOut<T>::value(Xb - Xa, a, b, xs, sc, fp64 != 0, ep);
         table[R.table_pos + r] = ce;
         // directory: buckets (bucket(prev start), bucket(this start)] -> r
         int bcur = ws_bucket((float)xs, R.lo, R.scale, nb);
@@ -777,8 +777,8 @@ __global__ void k_copy_sorted(const typename KeyOf<T>::K* __restrict__ sorted, c
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* lambdas, T* out, int32_t* ids,
-                          int64_t* n_clusters, int fp64, uint32_t* status, uint64_t spin_limit, int n_levels,
-                          cudaStream_t st) {
+                          int64_t* n_clusters, int fp64, const WsEpi& ep, uint32_t* status, uint64_t spin_limit,
+                          int n_levels, cudaStream_t st) {
     typedef typename KeyOf<T>::K K;
     if (W.n_lseg == 0) return cudaSuccess;
     K* sorted = nullptr;
@@ -807,7 +807,7 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
     WS_LAUNCH(W.prof, WSK_TABLE, st,
               (k_table<T><<<W.n_hull_tiles, 256, 0, st>>>(W.hull_tiles, W.lsegs, lambdas, W.rt, sorted, W.vp, W.vx,
                                                          W.pieces, W.npieces, W.tile_piece, W.table,
-                                                         W.dir, gaps, ngaps, gap_cap, fp64, status)));
+                                                         W.dir, gaps, ngaps, gap_cap, fp64, ep, status)));
     WS_LAUNCH(W.prof, WSK_BIG_GAPS, st, (k_big_gaps<<<1024, 256, 0, st>>>(gaps, ngaps, W.dir, gap_cap)));
     WS_LAUNCH(W.prof, WSK_LOOKUP, st,
               (k_lookup<T><<<W.n_sort_tiles, 256, 0, st>>>(values, W.sort_tiles, W.lsegs, W.rt, W.table, W.dir, out,
@@ -841,7 +841,7 @@ cudaError_t ws_large_copy_sorted(const LargeWork<T>& W, const typename KeyOf<T>:
 
 #define WS_INST(T)                                                                                                  \
     template cudaError_t ws_large_prox<T>(const LargeWork<T>&, const T*, const double*, T*, int32_t*, int64_t*, int, \
-                                          uint32_t*, uint64_t, int, cudaStream_t);                                  \
+                                          const WsEpi&, uint32_t*, uint64_t, int, cudaStream_t);                    \
     template cudaError_t ws_large_backward<T>(const LargeWork<T>&, const T*, const int32_t*, T*, uint32_t*,         \
                                               cudaStream_t);                                                        \
     template cudaError_t ws_large_copy_sorted<T>(const LargeWork<T>&, const typename KeyOf<T>::K*, T*, cudaStream_t);

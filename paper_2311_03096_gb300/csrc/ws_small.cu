@@ -45,7 +45,7 @@ template <typename T, int NT, int M>
 __global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, const int64_t* __restrict__ offsets,
                                               const int32_t* __restrict__ seg_list, const double* __restrict__ lambdas,
                                               T* out, int32_t* ids, int64_t* n_clusters, int fp64,
-                                              uint32_t* status) {
+                                              const WsEpi ep, uint32_t* status) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     typedef SmallSmem<T, NT, M> S;
@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, c
     }
     if (n == 1) {
         if (t == 0) {
-            out[a0] = values[a0];
+            const T x = values[a0];   // d = 1: no shift (the 1/(d-1) factor is vacuous)
+            out[a0] = fp64 ? (T)ws_epilogue<double>((double)x, 0.0, ep.beta, ep.gamma, ep.on != 0)
+                           : (T)ws_epilogue<float>((float)x, 0.0f, ep.beta_f, ep.gamma_f, ep.on != 0);
             if (ids) ids[a0] = 0;
             if (n_clusters) n_clusters[seg] = 1;
         }
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, c
     for (int r = t; r < c; r += NT) {
         const int a = s.r1.ids.V[r], b = s.r1.ids.V[r + 1];
         const T xs = (b - a == 1) ? values[a0 + s.idx[a]] : (T)0;
-        s.r2.val[r] = ValueOut<T>::value(X(b) - X(a), a, b, xs, sc, fp64 != 0);
+        s.r2.val[r] = ValueOut<T>::value(X(b) - X(a), a, b, xs, sc, fp64 != 0, ep);
         atomicOr(&s.r1.ids.mark[a >> 5], 1u << (a & 31));
     }
     __syncthreads();
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, 
 template <typename T>
 cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
                             const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
-                            uint32_t* status, cudaStream_t st, WsProf* prof) {
+                            const WsEpi& ep, uint32_t* status, cudaStream_t st, WsProf* prof) {
     constexpr int NT = 256;
     constexpr int M = SmallCfg<T>::M;
     if (n_list <= 0) return cudaSuccess;
@@ -252,7 +254,8 @@ cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     WS_LAUNCH(prof, WSK_SMALL, st,
-              (kern<<<n_list, NT, smem, st>>>(values, offsets, seg_list, lambdas, out, ids, n_clusters, fp64, status)));
+              (kern<<<n_list, NT, smem, st>>>(values, offsets, seg_list, lambdas, out, ids, n_clusters, fp64, ep,
+                                              status)));
     return cudaGetLastError();
 }
 
@@ -267,9 +270,10 @@ cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64
 }
 
 template cudaError_t ws_launch_small<float>(const float*, const int64_t*, const int32_t*, int, const double*, float*,
-                                            int32_t*, int64_t*, int, uint32_t*, cudaStream_t, WsProf*);
+                                            int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t, WsProf*);
 template cudaError_t ws_launch_small<double>(const double*, const int64_t*, const int32_t*, int, const double*,
-                                             double*, int32_t*, int64_t*, int, uint32_t*, cudaStream_t, WsProf*);
+                                             double*, int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t,
+                                             WsProf*);
 template cudaError_t ws_launch_small_backward<float>(const float*, const int32_t*, const int64_t*, const int32_t*,
                                                      int, float*, uint32_t*, cudaStream_t, WsProf*);
 template cudaError_t ws_launch_small_backward<double>(const double*, const int32_t*, const int64_t*,

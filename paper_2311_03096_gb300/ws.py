@@ -55,6 +55,9 @@ def _load():
             lib.ws_plan_destroy.restype = None
             lib.ws_prox_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
             lib.ws_prox.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]
+            lib.ws_prox_batched_l1.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+            lib.ws_prox_l1.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                       ctypes.c_int, _vp]
             lib.ws_prox_backward_batched.argtypes = [_vp, _vp, _vp, _vp, _vp]
             lib.ws_prox_backward.argtypes = [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, _vp]
             lib.ws_get_status.argtypes = [_vp, _vp]
@@ -181,6 +184,27 @@ def prox(w: torch.Tensor, lam: float, prec: str = "fp32comp", ids: bool = True, 
     return out, idt, nc
 
 
+class L1Rewind(ctypes.Structure):
+    """ws_l1_rewind: l1 coefficient beta, rewinding rho, displacement scale v_scale."""
+    _fields_ = [("beta", ctypes.c_double), ("rho", ctypes.c_double), ("v_scale", ctypes.c_double)]
+
+
+def prox_l1(w: torch.Tensor, lam: float, beta: float, rho: float = 0.0, v_scale: float = 1.0,
+            prec: str = "fp32comp", ids: bool = True, ctx: Context | None = None, out: torch.Tensor | None = None,
+            n_clusters: torch.Tensor | None = None, stream=None):
+    """Weight sharing + l1 with rewinding (Alg. 2) for one CUDA vector, through ws_prox_l1."""
+    if not w.is_cuda or w.dim() != 1 or not w.is_contiguous():
+        raise ValueError("w must be a contiguous 1-D CUDA tensor")
+    ctx = ctx or Context.get(w.device.index)
+    out = torch.empty_like(w) if out is None else out
+    idt = torch.empty(w.shape[0], dtype=torch.int32, device=w.device) if ids else None
+    nc = torch.zeros(1, dtype=torch.int64, device=w.device) if n_clusters is None else n_clusters
+    epi = L1Rewind(float(beta), float(rho), float(v_scale))
+    _check(_load().ws_prox_l1(ctx.handle, _ptr(w), w.shape[0], float(lam), ctypes.byref(epi), _ptr(out), _ptr(idt),
+                              _ptr(nc), _dtype_code(w.dtype), PREC[prec], _stream(stream)), "ws_prox_l1")
+    return out, idt, nc
+
+
 def prox_backward(grad_out: torch.Tensor, ids: torch.Tensor, ctx: Context | None = None, grad_in=None, stream=None):
     ctx = ctx or Context.get(grad_out.device.index)
     gin = torch.empty_like(grad_out) if grad_in is None else grad_in
@@ -233,6 +257,22 @@ class Plan:
             else n_clusters
         _check(_load().ws_prox_batched(self.handle, _ptr(values), _ptr(lambdas), _ptr(out), _ptr(idt), _ptr(nc),
                                        PREC[prec], _stream(stream)), "ws_prox_batched")
+        return out, idt, nc
+
+    def forward_l1(self, values: torch.Tensor, lambdas: torch.Tensor, beta: float, rho: float = 0.0,
+                   v_scale: float = 1.0, prec: str = "fp32comp", out=None, id_out=None, n_clusters=None, stream=None):
+        """Weight sharing + l1 with rewinding (Alg. 2) per segment, through ws_prox_batched_l1."""
+        if values.dtype != self.dtype or values.shape[0] != self.n or not values.is_cuda:
+            raise ValueError("values must be a CUDA tensor of the plan's dtype and length")
+        if lambdas.dtype != torch.float64 or lambdas.shape[0] != self.n_seg or not lambdas.is_cuda:
+            raise ValueError("lambdas must be a float64 CUDA tensor with one entry per segment")
+        out = torch.empty_like(values) if out is None else out
+        idt = torch.empty(self.n, dtype=torch.int32, device=values.device) if id_out is None else id_out
+        nc = torch.zeros(max(self.n_seg, 1), dtype=torch.int64, device=values.device) if n_clusters is None \
+            else n_clusters
+        epi = L1Rewind(float(beta), float(rho), float(v_scale))
+        _check(_load().ws_prox_batched_l1(self.handle, _ptr(values), _ptr(lambdas), ctypes.byref(epi), _ptr(out),
+                                          _ptr(idt), _ptr(nc), PREC[prec], _stream(stream)), "ws_prox_batched_l1")
         return out, idt, nc
 
     def backward(self, grad_out: torch.Tensor, ids: torch.Tensor, grad_in=None, stream=None):
