@@ -139,6 +139,21 @@ ws_status ws_prox_backward_batched(ws_plan* plan, const void* grad_out, const in
 ws_status ws_prox_backward(ws_ctx* ctx, const void* grad_out, const int32_t* cluster_ids, int64_t d,
                            void* grad_in, ws_dtype dtype, void* stream);
 
+/* R(w) and the weight-sharing measure of one vector of d weights (not part
+ * of the proximal step; for monitoring a model).  R(w) = 1/(d-1) *
+ * sum_{i>j} |w_i - w_j| (Eq. (1)) is evaluated as the appendix "Computing R"
+ * does: sort, then 1/(d-1) sum_k (2k - d - 1) x_k over the sorted x, the sum
+ * exact in 128-bit fixed point and rounded once (inputs spanning more than
+ * ~34 binades of FP32, or 5 of FP64, lose the bits of their smallest values
+ * below 2^-L, as the prox does).  The measure is #distinct nonzero weights /
+ * #nonzero weights (the weight-sharing metric of the CIFAR10 experiment), 0
+ * when every weight is zero.  w: DEVICE, d elements of dtype; R_out,
+ * metric_out: nullable DEVICE pointers to one double each.  d = 0 or 1 gives
+ * R = 0.  Plans (allocates) on first use of a (d, dtype); NaN/Inf inputs are
+ * reported through ws_get_status.  Stream-ordered. */
+ws_status ws_R(ws_ctx* ctx, const void* w, int64_t d, ws_dtype dtype, double* R_out, double* metric_out,
+               void* stream);
+
 /* Synchronise `stream`, then return and clear the context's device status
  * word (WS_OK if no device-side error happened since the last call). */
 ws_status ws_get_status(ws_ctx* ctx, void* stream);

@@ -140,6 +140,14 @@ def backward(grad_out, ids, offsets=None):
     return gin
 
 
+def ws_measure(w) -> float:
+    """Weight-sharing measure of the CIFAR10 experiment: #distinct nonzero weights /
+    #nonzero weights (0 when every weight is zero); -0.0 counts as zero."""
+    w = np.asarray(w, dtype=np.float64)
+    nz = w[w != 0]
+    return float(np.unique(nz).shape[0]) / float(nz.shape[0]) if nz.shape[0] else 0.0
+
+
 def R_pairs(w) -> float:
     """R(w) from Eq. (1), O(d^2)."""
     w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))

@@ -17,6 +17,7 @@ constexpr uint64_t WS_DEFAULT_SPIN = 1ull << 24;
 struct PlanCacheEntry {
     int64_t d;
     ws_dtype dtype;
+    int sort_only;   // every segment on the device-wide path (R and the measure need its sorted keys)
     ws_plan* plan;
 };
 
@@ -39,6 +40,7 @@ struct ws_plan {
     ws_dtype dtype = WS_F32;
     int64_t n = 0, n_seg = 0;
     int64_t small_max = 0;
+    bool sort_only = false;   // no one-CTA segments: everything takes the device-wide path
     std::vector<int64_t> h_offsets;
     int64_t* d_offsets = nullptr;
     int32_t* d_small = nullptr;
@@ -70,6 +72,7 @@ struct ws_plan {
     SegRuntime* rt = nullptr;
     void* table = nullptr;
     DirEntry* dir = nullptr;
+    void* stat_partial = nullptr;
     void* bsum = nullptr;
     int32_t* bcnt = nullptr;
 };
@@ -143,6 +146,7 @@ ws_status build_plan(ws_plan* p) {
     const int64_t small_cap = f64 ? SmallCfg<double>::CAP : SmallCfg<float>::CAP;
     p->small_max = p->ctx->small_max_override >= 0 ? std::min<int64_t>(p->ctx->small_max_override, small_cap)
                                                      : small_cap;
+    if (p->sort_only) p->small_max = 0;
     const size_t vsize = f64 ? 8 : 4, ksize = vsize;
     std::vector<int32_t> small;
     std::vector<LargeSeg> lsegs;
@@ -203,6 +207,7 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->tile_counter, sizeof(uint32_t) * P))) return st;
     if ((st = plan_alloc(p, (void**)&p->epoch, sizeof(uint32_t)))) return st;
     if ((st = plan_alloc(p, (void**)&p->seg_emin, sizeof(int32_t) * p->n_lseg))) return st;
+    if ((st = plan_alloc(p, &p->stat_partial, ws_R_partial_bytes(p->n_sort_tiles)))) return st;
     if (cudaMemset(p->epoch, 0, sizeof(uint32_t)) != cudaSuccess) return WS_ERR_CUDA;
     if (cudaMemset(p->lookback, 0, sizeof(uint64_t) * (size_t)P * p->n_sort_tiles * 256) != cudaSuccess)
         return WS_ERR_CUDA;
@@ -261,23 +266,55 @@ ws_status run_backward(ws_plan* p, const void* g, const int32_t* ids, void* gin,
     return WS_OK;
 }
 
-ws_plan* cached_plan(ws_ctx* ctx, int64_t d, ws_dtype dtype, ws_status* st) {
+ws_status plan_create_impl(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype,
+                           bool sort_only);
+
+ws_plan* cached_plan(ws_ctx* ctx, int64_t d, ws_dtype dtype, ws_status* st, int sort_only = 0) {
     std::lock_guard<std::mutex> g(ctx->mu);
     for (auto& c : ctx->cache)
-        if (c.d == d && c.dtype == dtype) { *st = WS_OK; return c.plan; }
+        if (c.d == d && c.dtype == dtype && c.sort_only == sort_only) { *st = WS_OK; return c.plan; }
     int64_t offs[2] = {0, d};
     ws_plan* p = nullptr;
-    *st = ws_plan_create(ctx, &p, offs, 1, dtype);
+    *st = plan_create_impl(ctx, &p, offs, 1, dtype, sort_only != 0);
     if (*st) return nullptr;
     if (ctx->cache.size() >= 8) {   // keep at most 8 cached shapes
         ws_plan_destroy(ctx->cache.front().plan);
         ctx->cache.erase(ctx->cache.begin());
     }
-    ctx->cache.push_back({d, dtype, p});
+    ctx->cache.push_back({d, dtype, sort_only, p});
     return p;
 }
 
+ws_status plan_create_impl(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype,
+                           bool sort_only) {
+    if (!ctx || !plan || n_seg < 0 || (n_seg > 0 && !offsets) || (dtype != WS_F32 && dtype != WS_F64))
+        return WS_ERR_INVALID;
+    *plan = nullptr;
+    if (n_seg > 0 && offsets[0] != 0) return WS_ERR_INVALID;
+    if (n_seg >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    for (int64_t s = 0; s < n_seg; ++s) {
+        int64_t len = offsets[s + 1] - offsets[s];
+        if (len < 0 || len >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return WS_ERR_CUDA;
+    ws_plan* p = new (std::nothrow) ws_plan();
+    if (!p) return WS_ERR_NOMEM;
+    p->ctx = ctx;
+    p->dtype = dtype;
+    p->sort_only = sort_only;
+    p->n_seg = n_seg;
+    p->h_offsets.assign(offsets ? offsets : nullptr, offsets ? offsets + n_seg + 1 : nullptr);
+    if (n_seg == 0) p->h_offsets.assign(1, 0);
+    p->n = p->h_offsets.back();
+    ws_status st = build_plan(p);
+    if (st) { ws_plan_destroy(p); return st; }
+    *plan = p;
+    return WS_OK;
+}
+
 }  // namespace
+
+
 
 extern "C" {
 
@@ -323,28 +360,7 @@ void ws_ctx_destroy(ws_ctx* ctx) {
 }
 
 ws_status ws_plan_create(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype) {
-    if (!ctx || !plan || n_seg < 0 || (n_seg > 0 && !offsets) || (dtype != WS_F32 && dtype != WS_F64))
-        return WS_ERR_INVALID;
-    *plan = nullptr;
-    if (n_seg > 0 && offsets[0] != 0) return WS_ERR_INVALID;
-    if (n_seg >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
-    for (int64_t s = 0; s < n_seg; ++s) {
-        int64_t len = offsets[s + 1] - offsets[s];
-        if (len < 0 || len >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
-    }
-    if (cudaSetDevice(ctx->device) != cudaSuccess) return WS_ERR_CUDA;
-    ws_plan* p = new (std::nothrow) ws_plan();
-    if (!p) return WS_ERR_NOMEM;
-    p->ctx = ctx;
-    p->dtype = dtype;
-    p->n_seg = n_seg;
-    p->h_offsets.assign(offsets ? offsets : nullptr, offsets ? offsets + n_seg + 1 : nullptr);
-    if (n_seg == 0) p->h_offsets.assign(1, 0);
-    p->n = p->h_offsets.back();
-    ws_status st = build_plan(p);
-    if (st) { ws_plan_destroy(p); return st; }
-    *plan = p;
-    return WS_OK;
+    return plan_create_impl(ctx, plan, offsets, n_seg, dtype, false);
 }
 
 void ws_plan_destroy(ws_plan* plan) {
@@ -440,6 +456,33 @@ ws_status ws_prox_backward(ws_ctx* ctx, const void* grad_out, const int32_t* clu
     ws_plan* p = cached_plan(ctx, d, dtype, &st);
     if (!p) return st;
     return ws_prox_backward_batched(p, grad_out, cluster_ids, grad_in, stream);
+}
+
+ws_status ws_R(ws_ctx* ctx, const void* w, int64_t d, ws_dtype dtype, double* R_out, double* metric_out,
+               void* stream) {
+    if (!ctx || d < 0 || (dtype != WS_F32 && dtype != WS_F64)) return WS_ERR_INVALID;
+    if (d >= ((int64_t)1 << 31) || (d > 0 && !w)) return WS_ERR_INVALID;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return WS_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (d <= 1) {
+        e = dtype == WS_F64 ? ws_tiny_R<double>((const double*)w, d, R_out, metric_out, &ctx->prof, st)
+                            : ws_tiny_R<float>((const float*)w, d, R_out, metric_out, &ctx->prof, st);
+        return map_cuda(e);
+    }
+    ws_status s;
+    ws_plan* p = cached_plan(ctx, d, dtype, &s, 1);
+    if (!p) return s;
+    if (dtype == WS_F64) {
+        LargeWork<double> W = make_work<double>(p);
+        e = ws_large_R<double>(W, (const double*)w, R_out, metric_out, ctx->status, ctx->spin_limit, p->stat_partial,
+                               st);
+    } else {
+        LargeWork<float> W = make_work<float>(p);
+        e = ws_large_R<float>(W, (const float*)w, R_out, metric_out, ctx->status, ctx->spin_limit, p->stat_partial,
+                              st);
+    }
+    return map_cuda(e);
 }
 
 ws_status ws_get_status(ws_ctx* ctx, void* stream) {

@@ -154,3 +154,11 @@ cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* 
                               cudaStream_t st);
 template <typename T>
 cudaError_t ws_large_copy_sorted(const LargeWork<T>& W, const typename KeyOf<T>::K* sorted, T* dst, cudaStream_t st);
+// R(w) and the weight-sharing measure per large segment (ws_stats.cu);
+// `partial` holds ws_R_partial_bytes(n_sort_tiles) bytes of device scratch.
+template <typename T>
+cudaError_t ws_large_R(const LargeWork<T>& W, const T* values, double* R_out, double* metric_out, uint32_t* status,
+                       uint64_t spin_limit, void* partial, cudaStream_t st);
+size_t ws_R_partial_bytes(int n_sort_tiles);
+template <typename T>
+cudaError_t ws_tiny_R(const T* values, int64_t d, double* R_out, double* metric_out, WsProf* prof, cudaStream_t st);

@@ -55,6 +55,7 @@ def _load():
             lib.ws_plan_destroy.restype = None
             lib.ws_prox_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
             lib.ws_prox.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]
+            lib.ws_R.argtypes = [_vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
             lib.ws_prox_batched_l1.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
             lib.ws_prox_l1.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
                                        ctypes.c_int, _vp]
@@ -182,6 +183,19 @@ def prox(w: torch.Tensor, lam: float, prec: str = "fp32comp", ids: bool = True, 
     _check(_load().ws_prox(ctx.handle, _ptr(w), w.shape[0], float(lam), _ptr(out), _ptr(idt), _ptr(nc),
                            _dtype_code(w.dtype), PREC[prec], _stream(stream)), "ws_prox")
     return out, idt, nc
+
+
+def R(w: torch.Tensor, ctx: Context | None = None, stream=None):
+    """R(w) (Eq. (1)) and the weight-sharing measure (#distinct nonzero / #nonzero) of one
+    CUDA vector, through ws_R.  Returns two float64 CUDA tensors of one element."""
+    if not w.is_cuda or w.dim() != 1 or not w.is_contiguous():
+        raise ValueError("w must be a contiguous 1-D CUDA tensor")
+    ctx = ctx or Context.get(w.device.index)
+    r = torch.empty(1, dtype=torch.float64, device=w.device)
+    m = torch.empty(1, dtype=torch.float64, device=w.device)
+    _check(_load().ws_R(ctx.handle, _ptr(w), w.shape[0], _dtype_code(w.dtype), _ptr(r), _ptr(m), _stream(stream)),
+           "ws_R")
+    return r, m
 
 
 class L1Rewind(ctypes.Structure):

@@ -388,3 +388,17 @@ def test_l1_rewind_rejects_bad_arguments():
     for args in ((-1.0, 0.0), (0.1, -0.5), (0.1, 1.5), (0.1, float("nan"))):
         with pytest.raises(oracle.OracleError):
             oracle.prox_l1(w, 0.1, args[0], args[1])
+
+
+# -- weight-sharing measure (CIFAR10 experiment) ----------------------------
+
+def test_ws_measure_definition():
+    assert oracle.ws_measure([0.0, -0.0, 1.0, 1.0, 2.0, -3.0]) == 3 / 4
+    assert oracle.ws_measure([0.0, 0.0]) == 0.0
+    assert oracle.ws_measure([5.0] * 10) == 0.1
+    rng = np.random.default_rng(41)
+    w = rng.standard_normal(1000)
+    assert oracle.ws_measure(w) == 1.0
+    assert oracle.ws_measure(rng.permutation(np.repeat(w[:10], 7))) == 10 / 70
+    out, _, nc = oracle.prox(w, 2.0)
+    assert oracle.ws_measure(out) == nc / np.count_nonzero(out)
