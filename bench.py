@@ -246,6 +246,10 @@ def bench_batched(ws, ctx, stream, reps=5):
             msg = _time_calls(g.replay, stream, reps)
             entry["graph_ms"] = msg
             entry["graph_elements_per_s"] = sub_off[-1] / (msg / 1e3)
+            tuned = ws.Plan.autotuned(sub_off, v, lt, "fp32comp", thresholds=[0, 1024, 2048, 4096], reps=2, ctx=ctx)
+            entry["autotune"] = {"threshold": tuned.threshold,
+                                 "ms_by_threshold": dict(zip(["0", "1024", "2048", "4096"], tuned.times_ms))}
+            del tuned
             ctx.check(what="bench batched")
             out_h, ids_h = out.cpu().numpy(), ids.cpu().numpy()
             rng = np.random.default_rng(7)

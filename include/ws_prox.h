@@ -84,6 +84,23 @@ ws_status ws_plan_create(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, in
                          ws_dtype dtype);
 void ws_plan_destroy(ws_plan* plan);
 
+/* Autotuned plan for a batch layout.  Segments of at most `threshold`
+ * elements run one CTA each (shared-memory sort and hull); longer ones run the
+ * device-wide tiled path.  For each candidate threshold (host array of n_cand
+ * values, each capped at the one-CTA maximum; NULL for {0, 512, 1024, 2048,
+ * 4096}) a plan is built and `reps` forward calls on (values, lambdas, out,
+ * cluster_ids, prec) are timed with CUDA events on `stream` after one
+ * warm-up; the fastest plan is returned in *plan and the others destroyed.
+ * *chosen (nullable) receives its threshold, times_ms (nullable, n_cand
+ * doubles) each candidate's mean milliseconds.  A set-up step: it allocates
+ * and synchronises the stream, so it is not capturable.  Arguments as for
+ * ws_plan_create and ws_prox_batched; reps >= 1, thresholds >= 0, else
+ * WS_ERR_INVALID.  Not in the paper: a library convenience. */
+ws_status ws_plan_autotune(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype,
+                           const void* values, const double* lambdas, void* out, int32_t* cluster_ids,
+                           ws_prec prec, const int64_t* thresholds, int n_cand, int reps, int64_t* chosen,
+                           double* times_ms, void* stream);
+
 /* Batched forward (Alg. 2 per segment, lambda = lambdas[s] from DEVICE memory,
  * n_seg doubles, each >= 0 and finite -- checked on the device, reported as
  * WS_ERR_INVALID through ws_get_status).  values/out: n elements of the

@@ -41,6 +41,7 @@ struct ws_plan {
     int64_t n = 0, n_seg = 0;
     int64_t small_max = 0;
     bool sort_only = false;   // no one-CTA segments: everything takes the device-wide path
+    int64_t small_force = -1; // >= 0: this plan's one-CTA length threshold (autotuned plans)
     std::vector<int64_t> h_offsets;
     int64_t* d_offsets = nullptr;
     int32_t* d_small = nullptr;
@@ -146,6 +147,7 @@ ws_status build_plan(ws_plan* p) {
     const int64_t small_cap = f64 ? SmallCfg<double>::CAP : SmallCfg<float>::CAP;
     p->small_max = p->ctx->small_max_override >= 0 ? std::min<int64_t>(p->ctx->small_max_override, small_cap)
                                                      : small_cap;
+    if (p->small_force >= 0) p->small_max = std::min<int64_t>(p->small_force, small_cap);
     if (p->sort_only) p->small_max = 0;
     const size_t vsize = f64 ? 8 : 4, ksize = vsize;
     std::vector<int32_t> small;
@@ -267,7 +269,7 @@ ws_status run_backward(ws_plan* p, const void* g, const int32_t* ids, void* gin,
 }
 
 ws_status plan_create_impl(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype,
-                           bool sort_only);
+                           bool sort_only, int64_t small_force = -1);
 
 ws_plan* cached_plan(ws_ctx* ctx, int64_t d, ws_dtype dtype, ws_status* st, int sort_only = 0) {
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -286,7 +288,7 @@ ws_plan* cached_plan(ws_ctx* ctx, int64_t d, ws_dtype dtype, ws_status* st, int 
 }
 
 ws_status plan_create_impl(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype,
-                           bool sort_only) {
+                           bool sort_only, int64_t small_force) {
     if (!ctx || !plan || n_seg < 0 || (n_seg > 0 && !offsets) || (dtype != WS_F32 && dtype != WS_F64))
         return WS_ERR_INVALID;
     *plan = nullptr;
@@ -302,6 +304,7 @@ ws_status plan_create_impl(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, 
     p->ctx = ctx;
     p->dtype = dtype;
     p->sort_only = sort_only;
+    p->small_force = small_force;
     p->n_seg = n_seg;
     p->h_offsets.assign(offsets ? offsets : nullptr, offsets ? offsets + n_seg + 1 : nullptr);
     if (n_seg == 0) p->h_offsets.assign(1, 0);
@@ -456,6 +459,54 @@ ws_status ws_prox_backward(ws_ctx* ctx, const void* grad_out, const int32_t* clu
     ws_plan* p = cached_plan(ctx, d, dtype, &st);
     if (!p) return st;
     return ws_prox_backward_batched(p, grad_out, cluster_ids, grad_in, stream);
+}
+
+ws_status ws_plan_autotune(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype,
+                           const void* values, const double* lambdas, void* out, int32_t* cluster_ids, ws_prec prec,
+                           const int64_t* thresholds, int n_cand, int reps, int64_t* chosen, double* times_ms,
+                           void* stream) {
+    static const int64_t kDefault[] = {0, 512, 1024, 2048, 4096};
+    if (!ctx || !plan || reps < 1) return WS_ERR_INVALID;
+    if (!thresholds) { thresholds = kDefault; n_cand = 5; }
+    if (n_cand < 1) return WS_ERR_INVALID;
+    *plan = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) { cudaGetLastError(); return WS_ERR_CUDA; }
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); cudaGetLastError(); return WS_ERR_CUDA; }
+    ws_plan* best = nullptr;
+    float best_ms = 0.0f;
+    int64_t best_t = -1;
+    ws_status rc = WS_OK;
+    for (int c = 0; c < n_cand && rc == WS_OK; ++c) {
+        if (thresholds[c] < 0) { rc = WS_ERR_INVALID; break; }
+        ws_plan* p = nullptr;
+        rc = plan_create_impl(ctx, &p, offsets, n_seg, dtype, false, thresholds[c]);
+        if (rc) break;
+        rc = ws_prox_batched(p, values, lambdas, out, cluster_ids, nullptr, prec, stream);   // warm-up
+        float ms = 0.0f;
+        if (rc == WS_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = WS_ERR_CUDA;
+        for (int r = 0; r < reps && rc == WS_OK; ++r)
+            rc = ws_prox_batched(p, values, lambdas, out, cluster_ids, nullptr, prec, stream);
+        if (rc == WS_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = WS_ERR_CUDA;
+        if (rc) { ws_plan_destroy(p); break; }
+        ms /= (float)reps;
+        if (times_ms) times_ms[c] = ms;
+        if (!best || ms < best_ms) {
+            if (best) ws_plan_destroy(best);
+            best = p; best_ms = ms; best_t = p->small_max;
+        } else {
+            ws_plan_destroy(p);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) { cudaGetLastError(); if (best) ws_plan_destroy(best); return rc; }
+    *plan = best;
+    if (chosen) *chosen = best_t;
+    return WS_OK;
 }
 
 ws_status ws_R(ws_ctx* ctx, const void* w, int64_t d, ws_dtype dtype, double* R_out, double* metric_out,

@@ -56,6 +56,8 @@ def _load():
             lib.ws_prox_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
             lib.ws_prox.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]
             lib.ws_R.argtypes = [_vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
+            lib.ws_plan_autotune.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                             _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
             lib.ws_prox_batched_l1.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
             lib.ws_prox_l1.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, _vp, ctypes.c_int,
                                        ctypes.c_int, _vp]
@@ -257,6 +259,32 @@ class Plan:
         _check(_load().ws_plan_create(self.ctx.handle, ctypes.byref(h), off.ctypes.data_as(_vp), self.n_seg,
                                       _dtype_code(dtype)), "ws_plan_create")
         self.handle = h
+
+    @classmethod
+    def autotuned(cls, offsets, values: torch.Tensor, lambdas: torch.Tensor, prec: str = "fp32comp",
+                  thresholds=None, reps: int = 3, ctx: Context | None = None, stream=None):
+        """Plan whose one-CTA / tiled length threshold is picked by timing (ws_plan_autotune).
+        Returns the plan; .threshold and .times_ms hold the choice and every candidate's time."""
+        self = cls.__new__(cls)
+        self.ctx = ctx or Context.get(values.device.index)
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        self.offsets, self.n_seg, self.n, self.dtype = off, off.shape[0] - 1, int(off[-1]), values.dtype
+        th = None if thresholds is None else np.ascontiguousarray(np.asarray(thresholds, dtype=np.int64))
+        n_cand = 5 if th is None else th.shape[0]
+        times = np.zeros(n_cand, np.float64)
+        chosen = ctypes.c_int64(-1)
+        out = torch.empty_like(values)
+        ids = torch.empty(self.n, dtype=torch.int32, device=values.device)
+        h = _vp()
+        _check(_load().ws_plan_autotune(self.ctx.handle, ctypes.byref(h), off.ctypes.data_as(_vp), self.n_seg,
+                                        _dtype_code(values.dtype), _ptr(values), _ptr(lambdas), _ptr(out), _ptr(ids),
+                                        PREC[prec], None if th is None else th.ctypes.data_as(_vp), n_cand, reps,
+                                        ctypes.byref(chosen), times.ctypes.data_as(_vp), _stream(stream)),
+               "ws_plan_autotune")
+        self.handle = h
+        self.threshold = int(chosen.value)
+        self.times_ms = times.tolist()
+        return self
 
     def forward(self, values: torch.Tensor, lambdas: torch.Tensor, prec: str = "fp32comp", ids: bool = True,
                 out=None, id_out=None, n_clusters=None, stream=None):

@@ -217,3 +217,18 @@ def test_spin_wait_gives_up(ws, ctx):
     w_np = inputs.normal(20000, seed=4, dtype=np.float32)
     out, ids, nc = run_one(ws, ctx, w_np, 0.5, "f32", "fp64")
     compare_segment(w_np, 0.5, out, ids, nc, 1e-5)
+
+
+def test_autotuned_plan_matches_default(ws, ctx):
+    vals, off, lam = _batched_case(21, n_seg=60, maxlen=9000)
+    v = torch.from_numpy(vals).cuda()
+    lt = torch.from_numpy(lam).cuda()
+    tuned = ws.Plan.autotuned(off, v, lt, "fp32comp", thresholds=[0, 1024, 4096], reps=2)
+    ctx.check(what="autotune")
+    assert tuned.threshold in (0, 1024, 4096) and len(tuned.times_ms) == 3 and min(tuned.times_ms) > 0
+    a = ws.Plan(off, torch.float32).forward(v, lt, "fp32comp")
+    b = tuned.forward(v, lt, "fp32comp")
+    ctx.check(what="autotuned forward")
+    # same exact partition whichever path a segment takes
+    assert torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+    assert float((a[0] - b[0]).abs().max()) <= 1e-5 * (1 + float(v.abs().max()) + float(lt.max()))
