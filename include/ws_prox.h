@@ -156,6 +156,22 @@ ws_status ws_prox_backward_batched(ws_plan* plan, const void* grad_out, const in
 ws_status ws_prox_backward(ws_ctx* ctx, const void* grad_out, const int32_t* cluster_ids, int64_t d,
                            void* grad_in, ws_dtype dtype, void* stream);
 
+/* Derivative with respect to lambda, the partition held fixed: a cluster on
+ * sorted positions a..b (1-based) moves with the mean velocity of its
+ * particles (Sec. 3), so d out_i / d lambda_s = (d+1-a-b)/(d-1) for every i in
+ * it (0 for segments of d <= 1).  grad_lambda[s] (DEVICE, n_seg doubles,
+ * overwritten) receives sum_{i in s} grad_out[i] * d out_i / d lambda_s,
+ * accumulated in FP64 with atomics (the order of the additions is not fixed).
+ * cluster_ids as written by the forward on the same plan layout (ranked by
+ * value, which is what fixes each cluster's positions).  grad_out: n elements
+ * of the plan's dtype.  Total of the plan's large-segment slots must be
+ * < 2^31, else WS_ERR_INVALID.  Stream-ordered. */
+ws_status ws_prox_dlambda_batched(ws_plan* plan, const void* grad_out, const int32_t* cluster_ids,
+                                  double* grad_lambda, void* stream);
+/* Single vector (plan cached as for ws_prox); grad_lambda: one DEVICE double. */
+ws_status ws_prox_dlambda(ws_ctx* ctx, const void* grad_out, const int32_t* cluster_ids, int64_t d,
+                          double* grad_lambda, ws_dtype dtype, void* stream);
+
 /* R(w) and the weight-sharing measure of one vector of d weights (not part
  * of the proximal step; for monitoring a model).  R(w) = 1/(d-1) *
  * sum_{i>j} |w_i - w_j| (Eq. (1)) is evaluated as the appendix "Computing R"

@@ -140,6 +140,31 @@ def backward(grad_out, ids, offsets=None):
     return gin
 
 
+def dlambda(grad_out, ids, offsets=None):
+    """Gradient of <grad_out, prox_{lam_s R}(w)> with respect to each segment's lam_s,
+    the partition held fixed: a cluster on sorted positions k = a..b (1-based) moves
+    with its mean velocity, d out / d lam = mean of (d + 1 - 2k)/(d - 1) over the
+    cluster = (d + 1 - a - b)/(d - 1) (Sec. 3 particle model; 0 when d <= 1).
+    Cluster r of a segment occupies the positions after clusters 0..r-1, so a and b
+    follow from the cluster sizes.  Returns one float64 per segment."""
+    g = np.asarray(grad_out, dtype=np.float64)
+    idv = np.asarray(ids, dtype=np.int64)
+    off = np.array([0, g.shape[0]], np.int64) if offsets is None else np.asarray(offsets, dtype=np.int64)
+    res = np.zeros(off.shape[0] - 1)
+    for s in range(off.shape[0] - 1):
+        a0, b0 = off[s], off[s + 1]
+        d = int(b0 - a0)
+        if d <= 1:
+            continue
+        r = idv[a0:b0]
+        size = np.bincount(r)
+        start = np.concatenate([[0], np.cumsum(size)[:-1]])       # 0-based first position
+        first, last = start + 1, start + size                      # 1-based a, b
+        dl = (d + 1 - first - last) / (d - 1)
+        res[s] = float(np.sum(g[a0:b0] * dl[r]))
+    return res
+
+
 def ws_measure(w) -> float:
     """Weight-sharing measure of the CIFAR10 experiment: #distinct nonzero weights /
     #nonzero weights (0 when every weight is zero); -0.0 counts as zero."""

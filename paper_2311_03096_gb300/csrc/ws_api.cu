@@ -461,6 +461,36 @@ ws_status ws_prox_backward(ws_ctx* ctx, const void* grad_out, const int32_t* clu
     return ws_prox_backward_batched(p, grad_out, cluster_ids, grad_in, stream);
 }
 
+ws_status ws_prox_dlambda_batched(ws_plan* plan, const void* grad_out, const int32_t* cluster_ids,
+                                  double* grad_lambda, void* stream) {
+    if (!plan || !grad_lambda) return WS_ERR_INVALID;
+    if (plan->n > 0 && (!grad_out || !cluster_ids)) return WS_ERR_INVALID;
+    if (plan->n_keys + plan->n_lseg >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    if (plan->n_seg == 0) return WS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (plan->dtype == WS_F64) {
+        LargeWork<double> W = make_work<double>(plan);
+        e = ws_dlambda<double>((const double*)grad_out, cluster_ids, plan->d_offsets, plan->d_small, plan->n_small,
+                               plan->n_seg, W, grad_lambda, plan->ctx->status, plan->stat_partial, st);
+    } else {
+        LargeWork<float> W = make_work<float>(plan);
+        e = ws_dlambda<float>((const float*)grad_out, cluster_ids, plan->d_offsets, plan->d_small, plan->n_small,
+                              plan->n_seg, W, grad_lambda, plan->ctx->status, plan->stat_partial, st);
+    }
+    return map_cuda(e);
+}
+
+ws_status ws_prox_dlambda(ws_ctx* ctx, const void* grad_out, const int32_t* cluster_ids, int64_t d,
+                          double* grad_lambda, ws_dtype dtype, void* stream) {
+    if (!ctx || d < 0 || (dtype != WS_F32 && dtype != WS_F64)) return WS_ERR_INVALID;
+    if (d >= ((int64_t)1 << 31)) return WS_ERR_INVALID;
+    ws_status st;
+    ws_plan* p = cached_plan(ctx, d, dtype, &st);
+    if (!p) return st;
+    return ws_prox_dlambda_batched(p, grad_out, cluster_ids, grad_lambda, stream);
+}
+
 ws_status ws_plan_autotune(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype,
                            const void* values, const double* lambdas, void* out, int32_t* cluster_ids, ws_prec prec,
                            const int64_t* thresholds, int n_cand, int reps, int64_t* chosen, double* times_ms,

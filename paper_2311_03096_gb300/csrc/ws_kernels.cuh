@@ -162,3 +162,9 @@ cudaError_t ws_large_R(const LargeWork<T>& W, const T* values, double* R_out, do
 size_t ws_R_partial_bytes(int n_sort_tiles);
 template <typename T>
 cudaError_t ws_tiny_R(const T* values, int64_t d, double* R_out, double* metric_out, WsProf* prof, cudaStream_t st);
+// d <grad_out, out> / d lambda per segment, partition held fixed (ws_stats.cu);
+// `partial` as for ws_large_R.
+template <typename T>
+cudaError_t ws_dlambda(const T* g, const int32_t* ids, const int64_t* d_offsets, const int32_t* d_small, int n_small,
+                       int64_t n_seg, const LargeWork<T>& W, double* out, uint32_t* status, void* partial,
+                       cudaStream_t st);

@@ -56,6 +56,8 @@ def _load():
             lib.ws_prox_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
             lib.ws_prox.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]
             lib.ws_R.argtypes = [_vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
+            lib.ws_prox_dlambda_batched.argtypes = [_vp, _vp, _vp, _vp, _vp]
+            lib.ws_prox_dlambda.argtypes = [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, _vp]
             lib.ws_plan_autotune.argtypes = [_vp, _vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
                                              _vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
             lib.ws_prox_batched_l1.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
@@ -185,6 +187,16 @@ def prox(w: torch.Tensor, lam: float, prec: str = "fp32comp", ids: bool = True, 
     _check(_load().ws_prox(ctx.handle, _ptr(w), w.shape[0], float(lam), _ptr(out), _ptr(idt), _ptr(nc),
                            _dtype_code(w.dtype), PREC[prec], _stream(stream)), "ws_prox")
     return out, idt, nc
+
+
+def prox_dlambda(grad_out: torch.Tensor, ids: torch.Tensor, ctx: Context | None = None, stream=None):
+    """sum_i grad_out[i] * d prox_i / d lambda (partition held fixed) for one vector, through
+    ws_prox_dlambda.  Returns a float64 CUDA tensor of one element."""
+    ctx = ctx or Context.get(grad_out.device.index)
+    res = torch.empty(1, dtype=torch.float64, device=grad_out.device)
+    _check(_load().ws_prox_dlambda(ctx.handle, _ptr(grad_out), _ptr(ids), grad_out.shape[0], _ptr(res),
+                                   _dtype_code(grad_out.dtype), _stream(stream)), "ws_prox_dlambda")
+    return res
 
 
 def R(w: torch.Tensor, ctx: Context | None = None, stream=None):
@@ -322,6 +334,13 @@ class Plan:
         _check(_load().ws_prox_backward_batched(self.handle, _ptr(grad_out), _ptr(ids), _ptr(gin), _stream(stream)),
                "ws_prox_backward_batched")
         return gin
+
+    def dlambda(self, grad_out: torch.Tensor, ids: torch.Tensor, stream=None):
+        """Per segment: sum_i grad_out[i] * d out_i / d lambda_s (ws_prox_dlambda_batched)."""
+        res = torch.empty(max(self.n_seg, 1), dtype=torch.float64, device=grad_out.device)
+        _check(_load().ws_prox_dlambda_batched(self.handle, _ptr(grad_out), _ptr(ids), _ptr(res), _stream(stream)),
+               "ws_prox_dlambda_batched")
+        return res[: self.n_seg]
 
     def debug_sort(self, values: torch.Tensor, sorted_out: torch.Tensor, stream=None):
         _check(_load().ws_debug_sort(self.handle, _ptr(values), _ptr(sorted_out), _stream(stream)), "ws_debug_sort")

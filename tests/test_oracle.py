@@ -402,3 +402,39 @@ def test_ws_measure_definition():
     assert oracle.ws_measure(rng.permutation(np.repeat(w[:10], 7))) == 10 / 70
     out, _, nc = oracle.prox(w, 2.0)
     assert oracle.ws_measure(out) == nc / np.count_nonzero(out)
+
+
+# -- d prox / d lambda (partition held fixed) ------------------------------
+
+def test_dlambda_matches_central_fd():
+    rng = np.random.default_rng(51)
+    for d, lam in ((2, 0.3), (64, 0.05), (500, 0.5), (3000, 2.0)):
+        w = rng.standard_normal(d)
+        g = rng.standard_normal(d)
+        out, ids, _ = oracle.prox(w, lam)
+        eps = 1e-7
+        ip, _, _ = oracle.prox(w, lam + eps)
+        im, _, _ = oracle.prox(w, lam - eps)
+        assert np.array_equal(oracle.prox(w, lam + eps)[1], ids) and np.array_equal(oracle.prox(w, lam - eps)[1], ids)
+        fd = (g @ ip - g @ im) / (2 * eps)
+        got = oracle.dlambda(g, ids)[0]
+        assert abs(got - fd) <= 1e-6 * (1 + abs(fd))
+
+
+def test_dlambda_batched_and_trivial_segments():
+    rng = np.random.default_rng(52)
+    lens = [0, 1, 5, 40]
+    off = np.concatenate([[0], np.cumsum(lens)])
+    w = rng.standard_normal(off[-1])
+    lam = np.array([0.1, 0.2, 0.3, 0.4])
+    out, ids, _ = oracle.prox_batched(w, off, lam)
+    g = rng.standard_normal(off[-1])
+    res = oracle.dlambda(g, ids, off)
+    assert res[0] == 0.0 and res[1] == 0.0
+    for s in (2, 3):
+        a, b = off[s], off[s + 1]
+        assert res[s] == oracle.dlambda(g[a:b], ids[a:b])[0]
+    # one cluster: every position moves with the mean velocity, which is 0
+    w1 = np.zeros(7)
+    o1, i1, n1 = oracle.prox(w1, 1.0)
+    assert n1 == 1 and abs(oracle.dlambda(rng.standard_normal(7), i1)[0]) < 1e-15
