@@ -44,10 +44,13 @@ ALGO_BYTES_PER_ELEM_F32 = {
     "lookup": 12,     # read w, write out and cluster id (I/O floor)
 }
 
-# DRAM traffic per launch from one ncu capture (profiles/*.txt) and the hash of
-# the kernel sources it was taken on; reported as null once the sources change.
-NCU_TRAFFIC = {}
-NCU_SOURCE_HASH = None
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture, and the hash of the kernel sources it was taken on; reported as
+# null once the sources change.  tile_hull: captured at d = 2^24 (lambda = 1),
+# 147.7 MB per launch, scaled by the element count to d = 2^26 (the kernel's
+# traffic grows with the elements it processes); see profiles/.
+NCU_TRAFFIC = {"tile_hull": 147.726e6 * 4}
+NCU_SOURCE_HASH = "49ca882d99accb49"
 
 
 def source_hash() -> str:
