@@ -109,15 +109,27 @@ __device__ int ws_tile_prefix(TilePrefix<NT, M>& tp, const typename KeyOf<T>::K 
     }
     binade_sh = sh;
     long long run = 0;
+    long long dq_last = 0;   // narrow: the chunk's last deviation (the others wait in s64, see below)
     if (mode == WS_TILE_BINADE) {
 #pragma unroll
         for (int i = 0; i < M; ++i)
             if (first + i < n) run += (long long)(kr[i] - k0);
+    } else if (mode == WS_TILE_NARROW) {
+        // deviation of element first+i parked at point first+i+1 of this chunk
+        // (overwritten by the prefix only after it has been read back)
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (first + i < n) {
+                const long long dq = ws_fixed<T>(KO::from_key(kr[i]), emax) - q0;
+                run += dq;
+                if (i + 1 < M) tp.s64[ws_sidx<M>(first + i + 1)] = dq;
+                else dq_last = dq;
+            }
+        }
     } else {
-        const int64_t sub = mode == WS_TILE_NARROW ? q0 : 0;
 #pragma unroll
         for (int i = 0; i < M; ++i)
-            if (first + i < n) run += ws_fixed<T>(KO::from_key(kr[i]), emax) - sub;
+            if (first + i < n) run += ws_fixed<T>(KO::from_key(kr[i]), emax);
     }
     if (mode != WS_TILE_WIDE) {
         long long tot;
@@ -125,10 +137,11 @@ __device__ int ws_tile_prefix(TilePrefix<NT, M>& tp, const typename KeyOf<T>::K 
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const int p = first + i;
+            long long dq = 0;
+            if (mode == WS_TILE_BINADE) dq = (long long)(kr[i] - k0);
+            else if (p < n) dq = (i + 1 < M) ? tp.s64[ws_sidx<M>(p + 1)] : dq_last;
             if (p <= n) tp.s64[ws_sidx<M>(p)] = acc;
-            if (p < n)
-                acc += (mode == WS_TILE_BINADE) ? (long long)(kr[i] - k0)
-                                                : ws_fixed<T>(KO::from_key(kr[i]), emax) - q0;
+            if (p < n) acc += dq;
         }
         if (t == 0 && n == CAP) tp.s64[ws_sidx<M>(CAP)] = tot;
         total_out = (mode == WS_TILE_BINADE) ? (i128)n * (i128)q0 + ((i128)tot << sh)

@@ -183,11 +183,27 @@ __global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, c
     const int c = nv - 1;
     if (s.r1.ids.V[0] != 0 || s.r1.ids.V[c] != n) { if (t == 0) ws_flag(status, WS_STATUS_INTERNAL); }
 
-    // ---- cluster values (a one-element cluster reads its weight back from the input)
+    // ---- cluster values (a one-element cluster reads its weight back from the input).
+    // FP32 arithmetic on deviation tiles: mean = x_first + (sum of deviations / n)
+    // 2^-L, all terms exact but the last conversions (error a few FP32 ulps of
+    // max |w|); otherwise from the exact 128-bit cluster sum.
+    const bool dev32 = !fp64 && mode != WS_TILE_WIDE;
+    const int Ldev = mode == WS_TILE_BINADE ? s.sct.L : sc.L;
+    const float x0f = (float)xlo;
     for (int r = t; r < c; r += NT) {
         const int a = s.r1.ids.V[r], b = s.r1.ids.V[r + 1];
         const T xs = (b - a == 1) ? values[a0 + s.idx[a]] : (T)0;
-        s.r2.val[r] = ValueOut<T>::value(X(b) - X(a), a, b, xs, sc, fp64 != 0, ep);
+        if (dev32) {
+            const float mean = (b - a == 1) ? (float)xs
+                                            : x0f + ldexpf(ws_u64_to_float((uint64_t)(s.pre.s64[ws_sidx<M>(b)] -
+                                                                                   s.pre.s64[ws_sidx<M>(a)])) /
+                                                               (float)(b - a),
+                                                           -Ldev);
+            s.r2.val[r] = (T)ws_epilogue<float>(mean, sc.mu_f * (float)(n - a - b), ep.beta_f, ep.gamma_f,
+                                                ep.on != 0);
+        } else {
+            s.r2.val[r] = ValueOut<T>::value(X(b) - X(a), a, b, xs, sc, fp64 != 0, ep);
+        }
         atomicOr(&s.r1.ids.mark[a >> 5], 1u << (a & 31));
     }
     __syncthreads();
