@@ -157,10 +157,11 @@ def run_reference(args, rank, world):
     oracle.build()
     w = inputs.normal_with_duplicates(args.d, seed=args.seed, dtype=np.float32)
     # size the per-step sample so that warmup + steps finish in about two minutes
-    probe = w[: 1 << 16]
+    probe = w[: 1 << 17]
     rate, _ = oracle_rate(probe, 3)
     budget = 120.0 / max(1, args.steps + args.warmup)
-    n = int(min(args.d, max(1 << 14, 2 ** int(np.log2(max(1.0, rate * budget))))))
+    # the oracle's rate falls slowly with n (the sort), so stay a power of two below the estimate
+    n = int(min(args.d, 1 << 22, max(1 << 14, 2 ** (int(np.log2(max(1.0, rate * budget))) - 1))))
     sample = w[:n]
     for k in range(args.warmup):
         oracle.prox(sample, LAMBDAS[k % 3])

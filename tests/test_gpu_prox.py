@@ -232,3 +232,45 @@ def test_autotuned_plan_matches_default(ws, ctx):
     # same exact partition whichever path a segment takes
     assert torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
     assert float((a[0] - b[0]).abs().max()) <= 1e-5 * (1 + float(v.abs().max()) + float(lt.max()))
+
+
+@pytest.mark.parametrize("path", ["one_cta", "device_wide"])
+def test_degenerate_and_extreme_inputs(ws, ctx, path):
+    """Constant vectors, sorted and reverse-sorted inputs, denormals and signed
+    zeros, values spanning ~60 binades, and extreme lambdas, on both paths."""
+    if path == "device_wide":
+        ctx.set_small_max(0)
+    rng = np.random.default_rng(77)
+    d = 3000 if path == "one_cta" else 300001
+    cases = []
+    cases.append(("constant", np.full(d, 0.37, np.float32), (0.0, 1e-3, 10.0)))
+    x = np.sort(rng.standard_normal(d)).astype(np.float32)
+    cases.append(("sorted", x, (1e-2, 1.0)))
+    cases.append(("reversed", x[::-1].copy(), (1e-2, 1.0)))
+    den = rng.standard_normal(d).astype(np.float32)
+    den[: d // 4] = (rng.integers(1, 1000, d // 4) * np.float32(1e-45)).astype(np.float32)   # denormals
+    den[d // 4: d // 4 + 50] = -0.0
+    cases.append(("denormals", den, (1e-30, 1e-3, 1.0)))
+    wide = (rng.standard_normal(d) * 10.0 ** rng.uniform(-4, 4, d)).astype(np.float32)   # ~27 binades: 128-bit tiles
+    cases.append(("wide_range", wide, (1e-3, 1e3)))
+    small = rng.standard_normal(d).astype(np.float32)
+    cases.append(("extreme_lambda", small, (1e-30, 1e6)))
+    for name, w_np, lams in cases:
+        for lam in lams:
+            out, ids, nc = run_one(ws, ctx, w_np, lam, "f32", "fp64")
+            compare_segment(w_np, lam, out, ids, nc, 1e-5)
+            if name == "constant":
+                assert nc == 1 and np.all(out == w_np[0])
+
+    # beyond the exact domain (values spanning ~200 binades): bits below 2^-L of the
+    # smallest values are dropped, so only the values and the structure of the
+    # partition are checked (ids rank the clusters in value order)
+    huge = (rng.standard_normal(d) * 10.0 ** rng.uniform(-30, 30, d)).astype(np.float32)
+    for lam in (1e-3, 1e3):
+        out, ids, nc = run_one(ws, ctx, huge, lam, "f32", "fp64")
+        ref, _, _ = oracle.prox(huge, lam)
+        scale = float(np.abs(huge).max()) + lam
+        assert float(np.abs(out.astype(np.float64) - ref).max()) <= 1e-5 * scale
+        order = np.argsort(huge, kind="stable")
+        g = ids[order]
+        assert g[0] == 0 and np.all(np.diff(g) >= 0) and np.all(np.diff(g) <= 1) and g[-1] == nc - 1
