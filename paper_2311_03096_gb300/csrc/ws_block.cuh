@@ -621,6 +621,15 @@ __device__ __forceinline__ void ws_merge_node(HullSmem<NT, M>& s, const Pts& P, 
     s.res_j[node] = js;
 }
 
+// Junction tests of the hull shortcuts (kept out of line: they run once per
+// thread and would otherwise add register pressure to the chain).
+template <class Pts>
+__device__ __noinline__ void ws_junction_checks(const Pts& P, const SegConst& sc, int first, int last, int next_last,
+                                                bool& conv_ok, bool& conc_ok) {
+    if (conv_ok) conv_ok = P.convex(last - 1, last, last + 1, sc);
+    if (conc_ok) conc_ok = !P.convex(first, last, next_last, sc);
+}
+
 // Build the hull of points 0..n of a tile.  Thread t owns chunk t = points
 // [t*M, min((t+1)*M, n)] and runs the sequential monotone chain (the stack
 // form of pool-adjacent-violators) over it; chunk hulls are then merged up a
@@ -656,9 +665,35 @@ __device__ void ws_cta_hull(HullSmem<NT, M>& s, int n, const Pts& P, const SegCo
     }
     s.lo[t] = 0;
     s.hi[t] = (uint16_t)cnt;
+    // ---- shortcuts (two hull tests per thread and two barriers):
+    //  * every chunk kept all its points and every junction triple is convex:
+    //    the tile is a convex sequence, its hull is every point;
+    //  * every chunk hull is its two end points and the chain of chunk end
+    //    points is concave at every junction: the hull is the chord (0, n).
+    bool skip_tree;
+    {
+        const int first = t * M;
+        bool conv_ok = true, conc_ok = true;
+        if (first < n) {
+            const int last = min(first + M, n);
+            conv_ok = cnt == last - first + 1;
+            conc_ok = cnt == 2;
+            if (last < n && (conv_ok || conc_ok))
+                ws_junction_checks<Pts>(P, sc, first, last, min(last + M, n), conv_ok, conc_ok);
+        }
+        const int all_conv = __syncthreads_and(conv_ok);
+        const int all_conc = __syncthreads_and(conc_ok);
+        skip_tree = all_conv || all_conc;
+        if (all_conv) {
+            if (t > 0 && first < n) s.lo[t] = 1;   // the junction point is the previous chunk's last
+        } else if (all_conc) {
+            if (t == 0) { s.H[0] = 0; s.H[NT] = (uint16_t)n; s.lo[0] = 0; s.hi[0] = 2; }
+            else { s.lo[t] = 0; s.hi[t] = 0; }
+        }
+    }
     __syncwarp();
     // ---- warp levels: chunks of one warp, warp-relative ranks
-    for (int half = 1; half < 32; half <<= 1) {
+    for (int half = skip_tree ? 32 : 1; half < 32; half <<= 1) {
         const int c = (int)s.hi[t] - (int)s.lo[t];
         const int inc = ws_warp_incl_scan<int>(c);
         s.cum[t] = inc - c;
@@ -674,7 +709,7 @@ __device__ void ws_cta_hull(HullSmem<NT, M>& s, int n, const Pts& P, const SegCo
         __syncwarp();
     }
     // ---- CTA levels
-    for (int half = 32; half < NT; half <<= 1) {
+    for (int half = skip_tree ? NT : 32; half < NT; half <<= 1) {
         const int c = (int)s.hi[t] - (int)s.lo[t];
         int tot;
         const int ex = ws_block_excl_scan<NT, int>(c, s.wsum_i, &tot);
