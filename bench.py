@@ -353,7 +353,7 @@ def main():
     import torch
 
     import __graft_entry__
-    from paper_2311_03096_gb300 import inputs, ws
+    from paper_2311_03096_gb300 import inputs, replicas, ws
 
     if world > 1:
         import torch.distributed as dist
@@ -385,8 +385,7 @@ def main():
     # ---- timed region: K steps, inputs resident in HBM
     ctx.profile(True)
     launches0 = ctx.launch_count()
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -397,19 +396,14 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     t_wall1 = time.time()
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     launches = ctx.launch_count() - launches0
     ms_total = e0.elapsed_time(e1)
     kern = ctx.profile_read()
     ctx.profile(False)
     ctx.check(what="bench timed region")
-    ms_max = ms_total
-    if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = args.d * args.steps * world / (ms_max / 1e3)
+    ms_max = replicas.max_over_ranks(ms_total, dev)
+    value = replicas.job_rate(args.d * args.steps, world, ms_max)
     ms_per_step = ms_max / args.steps
 
     # ---- dominant kernel roofline (live CUDA-event durations from the timed region)
@@ -444,8 +438,7 @@ def main():
             h_out.copy_(o, non_blocking=True)
             h_ids.copy_(i, non_blocking=True)
         torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -456,12 +449,8 @@ def main():
             h_ids.copy_(i, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
-        ms_e2e = f0.elapsed_time(f1)
-        if world > 1:
-            t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": args.d * n_e2e * world / (ms_e2e / 1e3), "unit": "elements/s",
+        ms_e2e = replicas.max_over_ranks(f0.elapsed_time(f1), dev)
+        e2e = {"value": replicas.job_rate(args.d * n_e2e, world, ms_e2e), "unit": "elements/s",
                "h2d_bytes_per_step": 4 * args.d, "d2h_bytes_per_step": 8 * args.d, "steps": n_e2e}
         ctx.check(what="bench e2e")
 
