@@ -611,8 +611,7 @@ ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, voi
 }
 
 static const char* const kKernelNames[WSK_COUNT] = {"small", "hist", "hist_scan", "onesweep", "tile_hull",
-                                                     "tile_scan", "merge", "root", "table", "big_gaps", "lookup",
-                                                     "backward", "misc"};
+                                                     "root", "table", "big_gaps", "lookup", "backward", "misc"};
 
 const char* ws_debug_kernel_name(int kind) {
     return (kind >= 0 && kind < WSK_COUNT) ? kKernelNames[kind] : nullptr;

@@ -188,7 +188,7 @@ __device__ __forceinline__ float ws_muq(double lam, const SegConst& sc, bool& us
 // NC contiguous runs ("chains") of ITEMS/NC items; each chain keeps its own
 // digit counters, so the NC read-modify-write chains through shared memory
 // are independent and overlap.  Within a chain, processing items in order
-// and lanes in order (match_any + popc) visits positions in order; chains
+// and lanes in order (peer mask + popc) visits positions in order; chains
 // and warps are combined in position order, so the ranking is stable.
 // Returns, per item, the position of the key in the digit-sorted tile;
 // digit_count/digit_start (shared, 256 entries) receive the tile histogram
@@ -301,41 +301,23 @@ struct HullSmem {
 // ---------------------------------------------------------------------------
 // The hull test on tile-local points.
 //
-// Narrow tiles: A, B are sums of deviations (q - q_0); the test
-// (B n1 - A n2) > mu 2^L (c - a) n1 n2 (the q_0 terms cancel) is decided in
-// FP32 with a rigorous error bound (each operand carries <= 2^-24 relative
-// rounding; the bound allows ~16 of them); only near-ties fall through to
-// the exact integer test.  Wide tiles: exact test only.
+// Wide tiles (prefix sums that need 128 bits): the exact integer test only.
+// Binade and narrow tiles (64-bit deviations from the tile's first point)
+// use TilePtsDev below.
 // ---------------------------------------------------------------------------
 static __device__ __noinline__ bool ws_convex_exact(i128 Xa, i128 Xb, i128 Xc, int a, int b, int c,
                                                     const SegConst& sc) {
     return ws_convex(Xa, Xb, Xc, a, b, c, sc);
 }
 
-template <int M, bool NARROW>
-struct TilePts {
-    const int64_t* s64;
-    const i128* base;
-    int64_t q0;
-    float muq;
-    bool fast;
+template <int M>
+struct TilePtsWide {
+    const int64_t* s64;   // chunk-relative prefix sums
+    const i128* base;     // prefix sum at each chunk start
     __device__ __forceinline__ int64_t v(int p) const { return s64[ws_sidx<M>(p)]; }
-    __device__ __forceinline__ i128 Xv(int p, int64_t vp) const {
-        return NARROW ? (i128)vp + (i128)p * (i128)q0 : base[p / M] + (i128)vp;
-    }
-    __device__ __forceinline__ i128 X(int p) const { return Xv(p, v(p)); }
+    __device__ __forceinline__ i128 Xv(int p, int64_t vp) const { return base[p / M] + (i128)vp; }
     __device__ __forceinline__ bool convex_v(int a, int64_t va, int b, int64_t vb, int c, int64_t vc,
                                              const SegConst& sc) const {
-        if (NARROW && fast) {
-            const float n1 = (float)(b - a), n2 = (float)(c - b);
-            const float fB = (float)(vc - vb) * n1;
-            const float fA = (float)(vb - va) * n2;
-            const float rhs = muq * (float)(c - a) * n1 * n2;
-            const float diff = (fB - fA) - rhs;
-            const float err = 1.0e-6f * (fabsf(fB) + fabsf(fA) + rhs);
-            if (diff > err) return true;
-            if (diff < -err) return false;
-        }
         return ws_convex_exact(Xv(a, va), Xv(b, vb), Xv(c, vc), a, b, c, sc);
     }
     __device__ __forceinline__ bool convex(int a, int b, int c, const SegConst& sc) const {
@@ -370,7 +352,7 @@ static __device__ __noinline__ bool ws_convex_binade_exact(int64_t A, int64_t B,
 // roundings (2^-24 each), mu, the product and the multiply add <= 4 to rhs,
 // the subtraction one more, < 3.1e-7 (Delta + rhs) in all; the 6e-7 margin
 // covers that.  Otherwise (FP64 keys spread over a wide range) the
-// filter runs on the rounded terms as in TilePts.  Near-ties fall through to
+// filter runs on the rounded terms.  Near-ties fall through to
 // the exact integer test.
 template <int M>
 struct TilePtsDev {

@@ -10,7 +10,7 @@ template <> struct SmallCfg<double> { static constexpr int M = 8; static constex
 // Opt-in per-launch timing (CUDA events recorded on the launching stream
 // around every kernel) and a launch counter.  Host-side only.
 enum WsKernelKind {
-    WSK_SMALL = 0, WSK_HIST, WSK_HIST_SCAN, WSK_ONESWEEP, WSK_TILE_HULL, WSK_TILE_SCAN, WSK_MERGE, WSK_ROOT,
+    WSK_SMALL = 0, WSK_HIST, WSK_HIST_SCAN, WSK_ONESWEEP, WSK_TILE_HULL, WSK_ROOT,
     WSK_TABLE, WSK_BIG_GAPS, WSK_LOOKUP, WSK_BWD, WSK_MISC, WSK_COUNT
 };
 struct WsProf {

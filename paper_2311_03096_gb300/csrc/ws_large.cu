@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(HNT, 3) k_tile_hull(const typename KeyOf<T>::K
         const TilePtsDev<HM> P = ws_dev_pts<HM>(s.pre.s64, s.muq, s.fast != 0, range, n, s.sc);
         ws_cta_hull<HNT, HM>(s.hull, n, P, s.sc, &nv);
     } else {
-        const TilePts<HM, false> P{s.pre.s64, s.pre.base, q0, 0.0f, false};
+        const TilePtsWide<HM> P{s.pre.s64, s.pre.base};
         ws_cta_hull<HNT, HM>(s.hull, n, P, s.sc, &nv);
     }
     {

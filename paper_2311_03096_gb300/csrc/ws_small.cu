@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, c
         const TilePtsDev<M> P = ws_dev_pts<M>(s.pre.s64, s.muq, s.fast != 0, range, n, sc);
         ws_cta_hull<NT, M>(s.r2.hull, n, P, sc, &nv);
     } else {
-        const TilePts<M, false> P{s.pre.s64, s.pre.base, q0, 0.0f, false};
+        const TilePtsWide<M> P{s.pre.s64, s.pre.base};
         ws_cta_hull<NT, M>(s.r2.hull, n, P, sc, &nv);
     }
     auto X = [&](int p) -> i128 { return ws_tile_X<M>(s.pre.s64, s.pre.base, mode, q0, bsh, p); };
