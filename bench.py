@@ -327,6 +327,8 @@ def bench_train(ws, ctx, stream, steps=10):
 
 def config_dict(args, world):
     return {"workload": WORKLOAD, "d": args.d, "lambdas": list(LAMBDAS), "storage": "f32", "prec": args.prec,
+            "arithmetic": "merge decisions exact in 64/128-bit fixed point; cluster values in "
+                          + ("FP32" if args.prec == "fp32comp" else "FP64"),
             "seed": args.seed, "l2": "inputs larger than L2 (256 MiB vector per step)",
             "parallelism": f"replicas x{world}"}
 
@@ -523,7 +525,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 values / i128 fixed-point sums", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32comp" else "f64", "data": "synthetic",
             "config": config_dict(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "kernels": shares, "variants": variants,
         }
