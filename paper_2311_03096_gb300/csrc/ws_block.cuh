@@ -603,6 +603,12 @@ __device__ __forceinline__ void ws_merge_node(HullSmem<NT, M>& s, const Pts& P, 
     s.res_j[node] = js;
 }
 
+// Is the junction point b a strict vertex between a and c?  (out of line)
+template <class Pts>
+__device__ __noinline__ bool ws_junction_convex(const Pts& P, const SegConst& sc, int a, int b, int c) {
+    return P.convex(a, b, c, sc);
+}
+
 // Junction tests of the hull shortcuts (kept out of line: they run once per
 // thread and would otherwise add register pressure to the chain).
 template <class Pts>
@@ -621,7 +627,7 @@ __device__ __noinline__ void ws_junction_checks(const Pts& P, const SegConst& sc
 // Sec. 4.3 / Thm 4.2, as a tangent search), so every chunk only narrows the
 // surviving range [lo, hi) of its own list.  On return s.cum is the CTA
 // exclusive scan of the surviving counts and *total_vertices their sum.
-template <int NT, int M, class Pts>
+template <int NT, int M, class Pts, bool JSKIP = false>
 __device__ void ws_cta_hull(HullSmem<NT, M>& s, int n, const Pts& P, const SegConst& sc, int* total_vertices) {
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     int cnt = 0;
@@ -673,9 +679,26 @@ __device__ void ws_cta_hull(HullSmem<NT, M>& s, int n, const Pts& P, const SegCo
             else { s.lo[t] = 0; s.hi[t] = 0; }
         }
     }
+    // ---- warp shortcut (JSKIP; pays off where most junctions are vertices,
+    // i.e. small lambda against the gaps): when every junction between the warp's chunks is a
+    // strict vertex of (its hull neighbour on the left, it, its hull neighbour
+    // on the right), the concatenated chunk hulls are a convex chain, hence
+    // the warp's hull: only the duplicated junction points go.
+    bool warp_skip = skip_tree;
+    if (JSKIP && !skip_tree) {
+        const int first = t * M;
+        bool jok = true;
+        if (lane < 31 && first + M < n) {
+            const int c0 = cnt, c1 = (int)s.hi[t + 1];
+            jok = c0 >= 2 && c1 >= 2 &&
+                  ws_junction_convex<Pts>(P, sc, (int)s.H[(c0 - 2) * NT + t], first + M, (int)s.H[NT + t + 1]);
+        }
+        warp_skip = __all_sync(WS_FULL_MASK, jok);
+        if (warp_skip && lane > 0 && first < n) s.lo[t] = 1;
+    }
     __syncwarp();
     // ---- warp levels: chunks of one warp, warp-relative ranks
-    for (int half = skip_tree ? 32 : 1; half < 32; half <<= 1) {
+    for (int half = warp_skip ? 32 : 1; half < 32; half <<= 1) {
         const int c = (int)s.hi[t] - (int)s.lo[t];
         const int inc = ws_warp_incl_scan<int>(c);
         s.cum[t] = inc - c;
@@ -690,8 +713,39 @@ __device__ void ws_cta_hull(HullSmem<NT, M>& s, int n, const Pts& P, const SegCo
         ws_apply_merge<NT, M>(s, t, node, half, nL, nR);
         __syncwarp();
     }
+    // ---- CTA shortcut: the same test at the junctions between warps
+    bool cta_skip = skip_tree;
+    if (JSKIP && !skip_tree && NT > 32) {
+        __syncthreads();
+        bool jok = true;
+        // lane 31 of warp w tests the junction J = end of warp w's range
+        const int J = (w + 1) * 32 * M;
+        const int has = (int)s.hi[t] - (int)s.lo[t];
+        const unsigned ne = __ballot_sync(WS_FULL_MASK, has > 0);
+        if (lane == 31 && w + 1 < NT / 32 && J < n) {
+            // left neighbour of J in warp w's hull: the vertex before J (J ends lane 31's list)
+            int left = -1;
+            if (has >= 2) left = (int)s.H[((int)s.hi[t] - 2) * NT + t];
+            else {
+                const unsigned before = ne & ((has >= 1) ? 0x7fffffffu : 0xffffffffu) & 0x7fffffffu;
+                if (before) { const int l = w * 32 + (31 - __clz(before)); left = (int)s.H[((int)s.hi[l] - 1) * NT + l]; }
+            }
+            // right neighbour: the second vertex of warp w+1's hull (its lane 0 list starts at J)
+            int right = -1;
+            const int t0 = (w + 1) * 32;
+            const int h0 = (int)s.hi[t0] - (int)s.lo[t0];
+            if (h0 >= 2) right = (int)s.H[((int)s.lo[t0] + 1) * NT + t0];
+            else {
+                for (int l = t0 + 1; l < t0 + 32 && l < NT; ++l)
+                    if (s.hi[l] > s.lo[l]) { right = (int)s.H[(int)s.lo[l] * NT + l]; break; }
+            }
+            jok = left >= 0 && right >= 0 && ws_junction_convex<Pts>(P, sc, left, J, right);
+        }
+        cta_skip = __syncthreads_and(jok);
+        if (cta_skip && lane == 0 && w > 0 && t * M < n && s.hi[t] > s.lo[t]) s.lo[t] = (uint16_t)(s.lo[t] + 1);
+    }
     // ---- CTA levels
-    for (int half = skip_tree ? NT : 32; half < NT; half <<= 1) {
+    for (int half = cta_skip ? NT : 32; half < NT; half <<= 1) {
         const int c = (int)s.hi[t] - (int)s.lo[t];
         int tot;
         const int ex = ws_block_excl_scan<NT, int>(c, s.wsum_i, &tot);

@@ -164,11 +164,11 @@ __global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, c
     if (mode == WS_TILE_BINADE) {
         const TilePtsDev<M> P =
             ws_dev_pts<M>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(klast - kfirst), n, s.sct);
-        ws_cta_hull<NT, M>(s.r2.hull, n, P, s.sct, &nv);
+        ws_cta_hull<NT, M, TilePtsDev<M>, true>(s.r2.hull, n, P, s.sct, &nv);
     } else if (mode == WS_TILE_NARROW) {
         const uint64_t range = (uint64_t)(ws_fixed<T>(xhi, emax) - q0);
         const TilePtsDev<M> P = ws_dev_pts<M>(s.pre.s64, s.muq, s.fast != 0, range, n, sc);
-        ws_cta_hull<NT, M>(s.r2.hull, n, P, sc, &nv);
+        ws_cta_hull<NT, M, TilePtsDev<M>, true>(s.r2.hull, n, P, sc, &nv);
     } else {
         const TilePtsWide<M> P{s.pre.s64, s.pre.base};
         ws_cta_hull<NT, M>(s.r2.hull, n, P, sc, &nv);
