@@ -426,34 +426,60 @@ def main():
             roofline = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
                         "ms_per_launch": ms_avg, "traffic": traffic}
 
-    # ---- end to end through the public API with host buffers (pinned)
+    # ---- end to end through the public API with host buffers (pinned).  Every step
+    # copies its input in and its result (values + ids) out; the copies of one step
+    # overlap the prox of the neighbouring steps (two buffers, copy engines on their
+    # own streams), as a pipelined caller would run it.
     e2e = None
     if not args.no_e2e:
         h_w = torch.from_numpy(w_np).pin_memory()
-        h_out = torch.empty(args.d, dtype=torch.float32).pin_memory()
-        h_ids = torch.empty(args.d, dtype=torch.int32).pin_memory()
-        d_w = torch.empty_like(w)
+        h_out = [torch.empty(args.d, dtype=torch.float32).pin_memory() for _ in range(2)]
+        h_ids = [torch.empty(args.d, dtype=torch.int32).pin_memory() for _ in range(2)]
+        d_w = [torch.empty_like(w) for _ in range(2)]
+        d_out = [out, torch.empty_like(w)]
+        d_ids = [ids, torch.empty_like(ids)]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
         n_e2e = max(3, min(args.steps, 50))
-        for k in range(2):
-            d_w.copy_(h_w, non_blocking=True)
-            o, i, _ = ws.prox(d_w, LAMBDAS[k % 3], args.prec, ctx=ctx, out=out, n_clusters=nc)
-            h_out.copy_(o, non_blocking=True)
-            h_ids.copy_(i, non_blocking=True)
+
+        def e2e_steps(count):
+            s_in.wait_stream(stream)    # nothing of these steps starts before the timer
+            s_out.wait_stream(stream)
+            done = [None, None]
+            for k in range(count):
+                b = k % 2
+                ev_free = torch.cuda.Event()
+                if done[b] is not None:
+                    s_in.wait_event(done[b])          # the buffer's previous step has been copied out
+                with torch.cuda.stream(s_in):
+                    d_w[b].copy_(h_w, non_blocking=True)
+                ev_in = torch.cuda.Event()
+                ev_in.record(s_in)
+                stream.wait_event(ev_in)
+                ws.prox(d_w[b], LAMBDAS[k % 3], args.prec, ctx=ctx, out=d_out[b], n_clusters=nc, stream=stream,
+                        id_out=d_ids[b])
+                ev_c = torch.cuda.Event()
+                ev_c.record(stream)
+                s_out.wait_event(ev_c)
+                with torch.cuda.stream(s_out):
+                    h_out[b].copy_(d_out[b], non_blocking=True)
+                    h_ids[b].copy_(d_ids[b], non_blocking=True)
+                ev_free.record(s_out)
+                done[b] = ev_free
+            stream.wait_stream(s_out)
+
+        e2e_steps(2)
         torch.cuda.synchronize()
         replicas.barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        for k in range(n_e2e):
-            d_w.copy_(h_w, non_blocking=True)
-            o, i, _ = ws.prox(d_w, LAMBDAS[k % 3], args.prec, ctx=ctx, out=out, n_clusters=nc)
-            h_out.copy_(o, non_blocking=True)
-            h_ids.copy_(i, non_blocking=True)
+        e2e_steps(n_e2e)
         f1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = replicas.max_over_ranks(f0.elapsed_time(f1), dev)
         e2e = {"value": replicas.job_rate(args.d * n_e2e, world, ms_e2e), "unit": "elements/s",
-               "h2d_bytes_per_step": 4 * args.d, "d2h_bytes_per_step": 8 * args.d, "steps": n_e2e}
+               "h2d_bytes_per_step": 4 * args.d, "d2h_bytes_per_step": 8 * args.d, "steps": n_e2e,
+               "pipelined": "copies of one step overlap the prox of the neighbouring steps (2 buffers)"}
         ctx.check(what="bench e2e")
 
     sampler.stop()

@@ -176,13 +176,15 @@ class Context:
 
 
 def prox(w: torch.Tensor, lam: float, prec: str = "fp32comp", ids: bool = True, ctx: Context | None = None,
-         out: torch.Tensor | None = None, n_clusters: torch.Tensor | None = None, stream=None):
+         out: torch.Tensor | None = None, n_clusters: torch.Tensor | None = None, stream=None,
+         id_out: torch.Tensor | None = None):
     """prox_{lam R}(w) for one CUDA vector.  Returns (out, ids or None, n_clusters int64 tensor[1])."""
     if not w.is_cuda or w.dim() != 1 or not w.is_contiguous():
         raise ValueError("w must be a contiguous 1-D CUDA tensor")
     ctx = ctx or Context.get(w.device.index)
     out = torch.empty_like(w) if out is None else out
-    idt = torch.empty(w.shape[0], dtype=torch.int32, device=w.device) if ids else None
+    idt = id_out if id_out is not None else \
+        (torch.empty(w.shape[0], dtype=torch.int32, device=w.device) if ids else None)
     nc = torch.zeros(1, dtype=torch.int64, device=w.device) if n_clusters is None else n_clusters
     _check(_load().ws_prox(ctx.handle, _ptr(w), w.shape[0], float(lam), _ptr(out), _ptr(idt), _ptr(nc),
                            _dtype_code(w.dtype), PREC[prec], _stream(stream)), "ws_prox")
