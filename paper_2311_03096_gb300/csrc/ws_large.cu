@@ -651,7 +651,8 @@ __device__ __forceinline__ int ws_find_cluster(const CEntry<T>* table, int64_t t
         const int mid = (l + h) >> 1;
         if (table[tp + mid].key <= k) l = mid + 1; else h = mid;
     }
-    out = table[tp + l - 1];
+    // key[jlo] <= k keeps l >= jlo + 1; the clamp only guards the read
+    out = table[tp + max(l - 1, jlo)];
     return l - 1;
 }
 
