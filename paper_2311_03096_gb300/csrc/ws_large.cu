@@ -236,17 +236,18 @@ __device__ __noinline__ void ws_merge_children(MergeSmem& m, Piece* pieces, int3
                 ok = false;
             }
             if (ok) {
+                // (the pieces named here are in the window: its copies, not global memory)
                 if (flag == 0) {   // junction stays: keep all of L, drop R_0
                     m.pl = npL - 1;
-                    const Piece qL = ws_ld_piece(PL + m.pl);
+                    const Piece qL = m.wpL[0];
                     m.is = qL.cum + (qL.hi - qL.lo) - 1;
                     m.js = 1;
                     if (nR >= 2) { m.pr = m.wRpc[1]; } else { m.pr = npR; }
                 } else {
                     m.pl = m.wLpc[li];
                     m.pr = m.wRpc[rj];
-                    const Piece qL = ws_ld_piece(PL + m.pl);
-                    const Piece qR = ws_ld_piece(PR + m.pr);
+                    const Piece qL = m.wpL[npL - 1 - m.pl];
+                    const Piece qR = m.wpR[m.pr];
                     m.is = qL.cum + (m.wLv[li] - qL.lo);
                     m.js = qR.cum + (m.wRv[rj] - qR.lo);
                 }
@@ -278,14 +279,17 @@ __device__ __noinline__ void ws_merge_children(MergeSmem& m, Piece* pieces, int3
             m.is = is; m.js = js;
         }
         if (m.pl >= 0 && m.is >= 0) {   // truncate the left list after istar
-            Piece q = ws_ld_piece(PL + m.pl);
+            const int slot = npL - 1 - m.pl;
+            Piece q = slot < m.nwpL ? m.wpL[slot] : ws_ld_piece(PL + m.pl);
             q.hi = (uint16_t)(q.lo + (m.is - q.cum) + 1);
             ws_st_piece(PL + m.pl, q);
         }
         if (m.pr < npR) {  // the right list starts at jstar
-            Piece q = ws_ld_piece(PR + m.pr);
+            const bool in_window = m.pr < m.nwpR;
+            Piece q = in_window ? m.wpR[m.pr] : ws_ld_piece(PR + m.pr);
             q.lo = (uint16_t)(q.lo + (m.js - q.cum));
             ws_st_piece(PR + m.pr, q);
+            if (in_window) m.wpR[m.pr] = q;   // the copy below reads the window
         }
     }
     __syncthreads();
@@ -300,7 +304,8 @@ __device__ __noinline__ void ws_merge_children(MergeSmem& m, Piece* pieces, int3
         Piece v;
         const bool has = b + t < keepR;
         if (has) {
-            v = ws_ld_piece(PR + firstR + b + t);
+            const int k = firstR + b + t;
+            v = k < m.nwpR ? m.wpR[k] : ws_ld_piece(PR + k);
             v.off += totL;
             v.cum = (b + t == 0) ? m.is + 1 : v.cum + shift;
         }
@@ -675,6 +680,14 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
     const DirEntry* D = dir + ls.dir_pos;
     const int64_t tp = R.table_pos;
     const int c = (int)R.n_clusters;
+    if (c == 1) {   // one cluster (large lambda): every weight gets its value, no search
+        const T v = table[tp].val;
+        for (int i = threadIdx.x; i < td.len; i += 256) {
+            __stcs(out + td.vpos + i, v);
+            if (ids) __stcs(ids + td.vpos + i, 0);
+        }
+        return;
+    }
     const uint64_t pol = ws_policy_evict_last();
     for (int i0 = threadIdx.x; i0 < td.len; i0 += 256 * LK) {
         T x[LK];
