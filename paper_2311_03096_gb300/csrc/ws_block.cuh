@@ -85,10 +85,24 @@ enum { WS_TILE_WIDE = 0, WS_TILE_NARROW = 1, WS_TILE_BINADE = 2 };
 //   NARROW: s64 holds D_p = sum (q_j - q_0) in global units.
 //   WIDE:   s64 holds chunk-relative prefixes, base[] the chunk starts (128-bit).
 // q0_out = global fixed-point image of element 0; total_out = X_n (global).
+// Is a tile with first/last keys k0, kn (n elements) a BINADE tile, and the
+// binade's shift sh against the segment scale (see ws_tile_prefix)?
+template <typename T>
+__device__ __forceinline__ bool ws_tile_binade(typename KeyOf<T>::K k0, typename KeyOf<T>::K kn, int n, int emax,
+                                               int& sh) {
+    typedef KeyOf<T> KO;
+    sh = ws_eff_exp(KO::from_key(k0)) - emax + KO::FIX_OFS;
+    const bool same_binade = ((k0 ^ kn) >> KO::MANT) == 0 && sh >= 0;
+    return same_binade && (uint64_t)(kn - k0) <= ((uint64_t)1 << 62) / (uint64_t)n;
+}
+
+// thr_dst/thr_val: an optional shared-memory store that is issued after the
+// prefix's first barrier (so it may overwrite storage that was read before
+// the call) and is visible to every thread on return.
 template <typename T, int NT, int M>
 __device__ int ws_tile_prefix(TilePrefix<NT, M>& tp, const typename KeyOf<T>::K (&kr)[M], typename KeyOf<T>::K k0,
                               typename KeyOf<T>::K kn, int n, int emax, int64_t& q0_out, i128& total_out,
-                              int& binade_sh) {
+                              int& binade_sh, int* thr_dst = nullptr, int thr_val = 0) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     constexpr int CAP = NT * M;
@@ -97,11 +111,10 @@ __device__ int ws_tile_prefix(TilePrefix<NT, M>& tp, const typename KeyOf<T>::K 
     const T x0 = KO::from_key(k0);
     const int64_t q0 = ws_fixed<T>(x0, emax);
     q0_out = q0;
-    const int sh = ws_eff_exp(x0) - emax + KO::FIX_OFS;
-    const bool same_binade = ((k0 ^ kn) >> KO::MANT) == 0 && sh >= 0;
-    const uint64_t krange = (uint64_t)(kn - k0);
+    int sh;
+    const bool binade = ws_tile_binade<T>(k0, kn, n, emax, sh);
     int mode;
-    if (same_binade && krange <= ((uint64_t)1 << 62) / (uint64_t)n) {
+    if (binade) {
         mode = WS_TILE_BINADE;
     } else {
         const int64_t qn = ws_fixed<T>(KO::from_key(kn), emax);
@@ -134,6 +147,7 @@ __device__ int ws_tile_prefix(TilePrefix<NT, M>& tp, const typename KeyOf<T>::K 
     if (mode != WS_TILE_WIDE) {
         long long tot;
         long long acc = ws_block_excl_scan<NT, long long>(run, tp.wsum64, &tot);
+        if (thr_dst) *thr_dst = thr_val;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const int p = first + i;
@@ -149,6 +163,7 @@ __device__ int ws_tile_prefix(TilePrefix<NT, M>& tp, const typename KeyOf<T>::K 
     } else {
         i128 tot;
         const i128 ex = ws_block_excl_scan<NT, i128>((i128)run, tp.wsum128, &tot);
+        if (thr_dst) *thr_dst = thr_val;
         long long acc = 0;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
@@ -296,6 +311,7 @@ struct HullSmem {
     int wtot[NT / 32];          // per-warp totals during the warp levels
     int res_i[NT], res_j[NT];
     int wsum_i[NT / 32];
+    int thr[M * M];             // chain thresholds (ws_thr_entry), indexed n1 * M + n2
 };
 
 // ---------------------------------------------------------------------------
@@ -312,6 +328,7 @@ static __device__ __noinline__ bool ws_convex_exact(i128 Xa, i128 Xb, i128 Xc, i
 
 template <int M>
 struct TilePtsWide {
+    static constexpr bool kThr = false;   // no chain thresholds
     const int64_t* s64;   // chunk-relative prefix sums
     const i128* base;     // prefix sum at each chunk start
     __device__ __forceinline__ int64_t v(int p) const { return s64[ws_sidx<M>(p)]; }
@@ -356,10 +373,12 @@ static __device__ __noinline__ bool ws_convex_binade_exact(int64_t A, int64_t B,
 // the exact integer test.
 template <int M>
 struct TilePtsDev {
+    static constexpr bool kThr = true;    // may carry chain thresholds
     const int64_t* s64;
     float muq;       // lambda 2^L_tile / (d - 1)
     bool fast;
     bool d64;        // range * n^2 <= 2^62: Delta is exact in 64 bits
+    const int* thr;  // chain thresholds (ws_thr_entry) or null
     uint64_t modd;   // lambda 2^L_tile = modd * 2^sodd with modd odd (0 if lambda = 0)
     int sodd;
     __device__ __forceinline__ int64_t v(int p) const { return s64[ws_sidx<M>(p)]; }
@@ -412,6 +431,62 @@ struct TilePtsDev {
     }
 };
 
+// Thresholds of the hull test inside one chunk.  Three points a < b < c of
+// one chunk have n1 = b - a and n2 = c - b in [1, M - 1], and the test is
+// Delta (d - 1) > mlam K 2^s with K = (n1 + n2) n1 n2 (lambda 2^L = mlam 2^s).
+// Delta is an integer, so this holds exactly when Delta > T with
+// T = floor(mlam K 2^s / (d - 1)); thr[n1 M + n2] = T, clamped to INT32_MAX,
+// turns the chain's test into one integer compare.  T is computed in integer
+// and FP32 arithmetic only (a float quotient, then exact remainder
+// corrections); entries with n1 + n2 > M are never read (0).
+__device__ __forceinline__ bool ws_gt_muK(int64_t D, uint64_t K, const SegConst& sc) {
+    return ws_convex_binade_exact(0, D, 1, 1, (int64_t)K, sc);   // D (d - 1) > mlam K 2^s
+}
+
+template <int M>
+__device__ __forceinline__ int ws_thr_entry(int i, uint64_t mlam, int s, uint64_t dm1) {
+    const int n1 = i / M, n2 = i % M;
+    if (!(n1 >= 1 && n2 >= 1 && n1 + n2 <= M) || mlam == 0) return 0;
+    const uint64_t K = (uint64_t)((n1 + n2) * n1 * n2);
+    const uint64_t N = mlam * K;   // mlam < 2^53, K <= M^3 / 4: N < 2^63
+    u128 Nn;                       // floor(N 2^s)
+    if (s >= 0) {
+        if (ws_bitlen64(N) - 1 + s >= ws_bitlen64(dm1) + 31) return INT32_MAX;   // N 2^s >= 2^31 (d - 1)
+        Nn = (u128)N << s;
+    } else {
+        Nn = (s <= -64) ? (u128)0 : (u128)(N >> -s);
+    }
+    if (Nn >= ((u128)dm1 << 31)) return INT32_MAX;
+    // T = floor(Nn / (d - 1)) < 2^31
+    const float fd = ws_u64_to_float(dm1);
+    float q = ws_i128_to_float_scaled((i128)Nn, 0) / fd;
+    int64_t T = (int64_t)fminf(fmaxf(q, 0.0f), 2147483648.0f);
+    i128 r = (i128)Nn - (i128)((u128)(uint64_t)T * (u128)dm1);
+    T += (int64_t)floorf(ws_i128_to_float_scaled(r, 0) / fd);   // |r / (d - 1)| < 2^10 here
+    r = (i128)Nn - (i128)T * (i128)dm1;
+    for (int it = 0; it < 4 && (r < 0 || r >= (i128)dm1); ++it) {
+        if (r < 0) { --T; r += (i128)dm1; } else { ++T; r -= (i128)dm1; }
+    }
+    if (r < 0 || r >= (i128)dm1) {   // not reached for the bounds above; exact bisection
+        SegConst c{};
+        c.mlam = mlam; c.s = s; c.dm1 = dm1;
+        int64_t lo = 0, hi = INT32_MAX;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo + 1) / 2;
+            if (ws_gt_muK(mid, K, c)) hi = mid - 1; else lo = mid;
+        }
+        T = lo;
+    }
+    return (int)min(T, (int64_t)INT32_MAX);
+}
+
+// Integer constants of the hull test at fixed-point scale 2^L, for ws_thr_entry.
+__device__ __forceinline__ void ws_thr_consts(double lam, int L, uint64_t& mlam, int& s) {
+    int elam;
+    ws_split_lambda(lam, mlam, elam);
+    s = elam + L;
+}
+
 // True when a tile of n points whose deviations span `range` keeps
 // B n1 - A n2 exact in 64 bits: |B n1|, |A n2| <= n1 n2 range <= n^2 range / 4.
 __device__ __forceinline__ bool ws_dev_d64(uint64_t range, int n) {
@@ -423,7 +498,7 @@ template <int M>
 __device__ __forceinline__ TilePtsDev<M> ws_dev_pts(const int64_t* s64, float muq, bool fast, uint64_t range, int n,
                                                     const SegConst& sc) {
     TilePtsDev<M> P;
-    P.s64 = s64; P.muq = muq; P.fast = fast; P.d64 = ws_dev_d64(range, n);
+    P.s64 = s64; P.muq = muq; P.fast = fast; P.d64 = ws_dev_d64(range, n); P.thr = nullptr;
     if (sc.mlam == 0) { P.modd = 0; P.sodd = 0; }
     else { const int tz = __ffsll((long long)sc.mlam) - 1; P.modd = sc.mlam >> tz; P.sodd = sc.s + tz; }
     return P;
@@ -633,7 +708,37 @@ __device__ void ws_cta_hull(HullSmem<NT, M>& s, int n, const Pts& P, const SegCo
     int cnt = 0;
     {
         const int first = t * M;
-        if (first < n) {
+        bool c32 = false;
+        if constexpr (Pts::kThr) {
+            // chunk span S: every Delta = B n1 - A n2 of the chunk is at most (M - 1) S
+            if (P.thr != nullptr && first < n)
+                c32 = (uint64_t)(P.v(min(first + M, n)) - P.v(first)) <= (uint64_t)(INT32_MAX - 1) / (M - 1);
+        }
+        if (c32) {
+            if constexpr (Pts::kThr) {
+                // exact 32-bit chain: A, B and Delta are exact in 32 bits (differences of
+                // the low words), the right-hand side is the threshold table
+                const int32_t* w32 = reinterpret_cast<const int32_t*>(P.s64);
+                const int last = min(first + M, n);
+                int p0 = 0, p1 = 0;
+                uint32_t r0 = 0, r1 = 0;
+                for (int pnt = first; pnt <= last; ++pnt) {
+                    const uint32_t rp = (uint32_t)w32[2 * ws_sidx<M>(pnt)];
+                    while (cnt >= 2) {
+                        const int n1 = p1 - p0, n2 = pnt - p1;
+                        const int D = (int)((rp - r1) * (uint32_t)n1 - (r1 - r0) * (uint32_t)n2);
+                        if (D > P.thr[n1 * M + n2]) break;
+                        --cnt;
+                        p1 = p0; r1 = r0;
+                        if (cnt >= 2) { p0 = s.H[(cnt - 2) * NT + t]; r0 = (uint32_t)w32[2 * ws_sidx<M>(p0)]; }
+                    }
+                    s.H[cnt * NT + t] = (uint16_t)pnt;
+                    p0 = p1; r0 = r1;
+                    p1 = pnt; r1 = rp;
+                    ++cnt;
+                }
+            }
+        } else if (first < n) {
             const int last = min(first + M, n);
             int p0 = 0, p1 = 0;          // the two top entries of the stack
             int64_t v0 = 0, v1 = 0;

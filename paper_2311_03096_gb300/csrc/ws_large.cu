@@ -390,18 +390,32 @@ __global__ void __launch_bounds__(HNT, 3) k_tile_hull(const typename KeyOf<T>::K
             for (int i = 0; i < HM; ++i) kr[i] = (first + i < n) ? src[i] : (K)0;
         }
     }
+    // this thread's entry of the chain thresholds, at the scale the tile's mode uses
+    // (computed while the keys are in flight; stored by the prefix after its first barrier)
+    static_assert(HM * HM <= HNT, "one threshold entry per thread");
+    int thr_v = 0;
+    if (t < HM * HM) {
+        int shb;
+        const bool tbin = ws_tile_binade<T>(kfirst, klast, n, emax, shb);
+        uint64_t mlam;
+        int sx;
+        ws_thr_consts(lamv, KO::L_BASE - emax - (tbin && shb > 0 ? shb : 0), mlam, sx);
+        thr_v = ws_thr_entry<HM>(t, mlam, sx, ls.len > 1 ? (uint64_t)(ls.len - 1) : 1ull);
+    }
     int64_t q0;
     i128 total;
     int bsh;
-    const int mode = ws_tile_prefix<T, HNT, HM>(s.pre, kr, kfirst, klast, n, emax, q0, total, bsh);
+    const int mode = ws_tile_prefix<T, HNT, HM>(s.pre, kr, kfirst, klast, n, emax, q0, total, bsh,
+                                                t < HM * HM ? s.hull.thr + t : nullptr, thr_v);
     int nv;
     if (mode == WS_TILE_BINADE) {
-        const TilePtsDev<HM> P =
-            ws_dev_pts<HM>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(klast - kfirst), n, s.sct);
+        TilePtsDev<HM> P = ws_dev_pts<HM>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(klast - kfirst), n, s.sct);
+        P.thr = s.hull.thr;
         ws_cta_hull<HNT, HM>(s.hull, n, P, s.sct, &nv);
     } else if (mode == WS_TILE_NARROW) {
         const uint64_t range = (uint64_t)(ws_fixed<T>(KO::from_key(klast), emax) - q0);
-        const TilePtsDev<HM> P = ws_dev_pts<HM>(s.pre.s64, s.muq, s.fast != 0, range, n, s.sc);
+        TilePtsDev<HM> P = ws_dev_pts<HM>(s.pre.s64, s.muq, s.fast != 0, range, n, s.sc);
+        P.thr = s.hull.thr;
         ws_cta_hull<HNT, HM>(s.hull, n, P, s.sc, &nv);
     } else {
         const TilePtsWide<HM> P{s.pre.s64, s.pre.base};

@@ -156,18 +156,32 @@ __global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, c
         s.fastt = f ? 1 : 0;
     }
     // (the prefix sums end with a barrier; the keys' storage is reused from here on)
-    const int mode = ws_tile_prefix<T, NT, M>(s.pre, kr, kfirst, klast, n, emax, q0, total, bsh);
+    // this thread's entry of the chain thresholds at the scale the segment's mode
+    // uses; the prefix stores it after its first barrier (the keys are dead then)
+    static_assert(M * M <= NT, "one threshold entry per thread");
+    int thr_v = 0;
+    if (t < M * M) {
+        int shb;
+        const bool tbin = ws_tile_binade<T>(kfirst, klast, n, emax, shb);
+        uint64_t mlam;
+        int sx;
+        ws_thr_consts(lam, KO::L_BASE - emax - (tbin && shb > 0 ? shb : 0), mlam, sx);
+        thr_v = ws_thr_entry<M>(t, mlam, sx, n > 1 ? (uint64_t)(n - 1) : 1ull);
+    }
+    const int mode = ws_tile_prefix<T, NT, M>(s.pre, kr, kfirst, klast, n, emax, q0, total, bsh,
+                                              t < M * M ? s.r2.hull.thr + t : nullptr, thr_v);
     const SegConst& sc = s.sc;
 
     // ---- exact hull (in-CTA merge)
     int nv;
     if (mode == WS_TILE_BINADE) {
-        const TilePtsDev<M> P =
-            ws_dev_pts<M>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(klast - kfirst), n, s.sct);
+        TilePtsDev<M> P = ws_dev_pts<M>(s.pre.s64, s.muqt, s.fastt != 0, (uint64_t)(klast - kfirst), n, s.sct);
+        P.thr = s.r2.hull.thr;
         ws_cta_hull<NT, M, TilePtsDev<M>, true>(s.r2.hull, n, P, s.sct, &nv);
     } else if (mode == WS_TILE_NARROW) {
         const uint64_t range = (uint64_t)(ws_fixed<T>(xhi, emax) - q0);
-        const TilePtsDev<M> P = ws_dev_pts<M>(s.pre.s64, s.muq, s.fast != 0, range, n, sc);
+        TilePtsDev<M> P = ws_dev_pts<M>(s.pre.s64, s.muq, s.fast != 0, range, n, sc);
+        P.thr = s.r2.hull.thr;
         ws_cta_hull<NT, M, TilePtsDev<M>, true>(s.r2.hull, n, P, sc, &nv);
     } else {
         const TilePtsWide<M> P{s.pre.s64, s.pre.base};
