@@ -269,10 +269,15 @@ __device__ __forceinline__ float ws_i128_to_float_scaled(i128 v, int neg_exp) {
     const float f = ws_u64_to_float((uint64_t)(mag >> sh));
     return ldexpf(v < 0 ? -f : f, sh - neg_exp);
 }
+// Magnitude first, sign last: the halves of a negative two's-complement value
+// would cancel (hi = -1, lo ~ 2^64 - |v|) and lose the low bits of |v|.
+// hi converts exactly while |v| < 2^117; lo rounds once and the fused add
+// once more: <= 2 roundings relative to |v|.
 __device__ __forceinline__ double ws_i128_to_double(i128 v) {
-    long long hi = (long long)(v >> 64);
-    unsigned long long lo = (unsigned long long)(uint64_t)v;
-    return fma(__ll2double_rn(hi), 18446744073709551616.0, __ull2double_rn(lo));
+    const bool neg = v < 0;
+    const u128 m = neg ? (u128)0 - (u128)v : (u128)v;
+    const double r = fma(__ull2double_rn((uint64_t)(m >> 64)), 18446744073709551616.0, __ull2double_rn((uint64_t)m));
+    return neg ? -r : r;
 }
 
 // Weight sharing + l1 with rewinding (Rewinding section, Alg. 2): a cluster

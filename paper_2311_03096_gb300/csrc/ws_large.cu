@@ -743,17 +743,16 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
         }
 #pragma unroll
         for (int u = 0; u < LK; ++u) {
+            if (!in[u]) continue;   // past the tile's end: no element (its x = 0 may precede every cluster)
             CEntry<T> ce;
             const int jlo = max(lo[u] - 1, 0), jhi = max(hi[u] - 1, jlo);
             int r = jlo;
             if (jhi == jlo) ce = table[tp + jlo];   // one candidate: no search
             else r = ws_find_cluster<T>(table, tp, jlo, jhi, g[u], k[u], ce);
             if (r < 0 || r >= c) { ws_flag(status, WS_STATUS_INTERNAL); r = 0; ce = table[tp]; }
-            if (in[u]) {
-                const int i = i0 + u * 256;
-                __stcs(out + td.vpos + i, ce.val);
-                if (ids) __stcs(ids + td.vpos + i, r);
-            }
+            const int i = i0 + u * 256;
+            __stcs(out + td.vpos + i, ce.val);
+            if (ids) __stcs(ids + td.vpos + i, r);
         }
     }
 }

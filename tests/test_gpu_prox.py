@@ -274,3 +274,19 @@ def test_degenerate_and_extreme_inputs(ws, ctx, path):
         order = np.argsort(huge, kind="stable")
         g = ids[order]
         assert g[0] == 0 and np.all(np.diff(g) >= 0) and np.all(np.diff(g) <= 1) and g[-1] == nc - 1
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("d", [37, 5001, 300001])
+def test_one_signed_inputs_device_wide(ws, ctx, dt, d):
+    """All-positive and all-negative vectors on the device-wide path at ragged
+    sizes: lanes past a tile's end carry no element, and their placeholder
+    value 0 lies outside the data range (before every cluster or after the
+    last one); the device status must stay clean."""
+    ctx.set_small_max(0)
+    base = inputs.normal_with_duplicates(d, seed=d + 9, dtype=NP[dt])
+    for shift in (6.0, -6.0):
+        w_np = (base + NP[dt](shift)).astype(NP[dt])
+        for lam in (1e-3, 0.5):
+            out, ids, nc = run_one(ws, ctx, w_np, lam, dt, "fp64")
+            compare_segment(w_np, lam, out, ids, nc, TOL[(dt, "fp64")])
