@@ -15,6 +15,8 @@ Workloads (sizes as used by the tests and the benchmark):
                     left block absorbs the right half one particle per round.
   * ``mirror``      pairs of exact duplicates, 3h or 4h apart, with
                     lambda = 0.75 h (d - 1)/2: d/2 independent two-particle merges.
+  * ``tie_lattice`` values on a lattice of one unit with lambda set so the
+                    shift drops one unit per position: dense exact ties.
   * ``mlp``         Kaiming-uniform weights of an MLP 3072-4096-4096-10 split
                     into per-row segments, whole-layer segments and extra
                     segments with log-uniform lengths (batched workload).
@@ -87,6 +89,25 @@ def mirror(d: int, seed: int = 0, shuffle: bool = False):
         w = w[rng.permutation(d)]
     lam = 0.75 * H_CASCADE * (d - 1) / 2.0
     return w, lam
+
+
+def tie_lattice(d: int, seed: int = 0, dtype=np.float32, binade: bool = True, shuffle: bool = True):
+    """Values on a lattice of one unit u = 2^-(p-1) (p = 24 for float, 53 for
+    double): w = base + n u with n a random walk of steps 0 to 3 (base = 1,
+    one binade, or base = 0, spanning binades), and lam = (d - 1) u / 2, so the
+    shift drops by exactly one unit per sorted position.  Every sum the prox
+    compares is then an integer multiple of u / 2, and steps of one unit are
+    exact ties of adjacent block means.  Returns (w, lam, n) with n the integer
+    lattice index of every w (same order)."""
+    p = 24 if np.dtype(dtype) == np.float32 else 53
+    rng = _rng(seed)
+    n = np.cumsum(rng.integers(0, 4, d)).astype(np.int64)
+    if shuffle:
+        n = n[rng.permutation(d)]
+    base = 1.0 if binade else 0.0
+    w = (base + n.astype(np.float64) * 2.0 ** -(p - 1)).astype(dtype)
+    lam = (d - 1) * 2.0 ** -p
+    return w, lam, n
 
 
 MLP_SIZES = (3072, 4096, 4096, 10)

@@ -53,3 +53,35 @@ def compare_segment(w, lam, out_gpu, ids_gpu, nc_gpu, tol, ref=None):
     diag["rel_err"] = err / scale if scale > 0 else err
     assert err <= tol * scale, f"max |gpu - oracle| = {err:.3e} > {tol:.0e} * {scale:.3e}"
     return diag
+
+
+def integer_pav(Y):
+    """PAV of integers y in sorted order, pooling while mean(below) >= mean(top)
+    (Sec. 4.1: ties pool); means compared by exact cross-multiplication.
+    Returns the block starts, sums and counts."""
+    starts, sums, cnts = [], [], []
+    for k, yk in enumerate(Y.tolist()):
+        starts.append(k)
+        sums.append(yk)
+        cnts.append(1)
+        while len(sums) >= 2 and sums[-2] * cnts[-1] >= sums[-1] * cnts[-2]:
+            s, c = sums.pop(), cnts.pop()
+            starts.pop()
+            sums[-1] += s
+            cnts[-1] += c
+    return np.array(starts, np.int64), sums, cnts
+
+
+def lattice_expected(n, d):
+    """Exact prox partition of a tie lattice (inputs.tie_lattice) from its integer
+    indices n: 2 (y_k - base) / u = 2 n_k + d + 1 - 2k.  Returns the cluster id
+    of every element (input order), the cluster mean of those integers for every
+    element (value = base + mean * u / 2) and the cluster count."""
+    perm = np.argsort(n, kind="stable")
+    Y = 2 * n[perm] + (d + 1) - 2 * np.arange(1, d + 1, dtype=np.int64)
+    starts, sums, cnts = integer_pav(Y)
+    ids = np.empty(d, np.int32)
+    ids[perm] = np.repeat(np.arange(len(starts), dtype=np.int32), cnts)
+    means = np.empty(d, np.float64)
+    means[perm] = np.repeat(np.array([s / c for s, c in zip(sums, cnts)]), cnts)
+    return ids, means, len(starts)

@@ -262,6 +262,21 @@ def test_mirror_generator(d):
     assert np.all(np.bincount(ids) == 2)
 
 
+@pytest.mark.parametrize("binade", [True, False])
+@pytest.mark.parametrize("d", [37, 4096, 70001])
+def test_tie_lattice_matches_integer_pav(d, binade):
+    # exact ties everywhere (steps of one unit tie adjacent block means); for
+    # float inputs every y and every block sum is exact in FP64, so the oracle
+    # must pool exactly where integer PAV with >= pooling does (Sec. 4.1)
+    from parity import lattice_expected
+    w, lam, n = inputs.tie_lattice(d, seed=d % 97 + 3, binade=binade)
+    ids_ref, means, nc_ref = lattice_expected(n, d)
+    out, ids, nc = oracle.prox(w, lam)
+    assert nc == nc_ref
+    assert np.array_equal(ids, ids_ref)
+    np.testing.assert_array_equal(out, (1.0 if binade else 0.0) + means * 2.0 ** -24)
+
+
 def test_backward_is_cluster_average_and_matches_fd():
     rng = np.random.default_rng(4)
     d, lam, eps = 64, 0.05, 1e-6
