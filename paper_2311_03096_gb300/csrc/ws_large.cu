@@ -152,7 +152,145 @@ struct MergeSmem {
     int64_t wLpt[MW], wRpt[MW];
     i128 wLX[MW], wRX[MW];
     int ok;
+    int cand_i[HNT / 32], cand_s[HNT / 32], cand_j[HNT / 32];   // parallel search: one candidate per warp
 };
+
+// Vertex of rank r of a node hull whose piece list is cached in shared memory.
+__device__ __forceinline__ void ws_cached_vertex(const Piece* c, int np, int r, const uint16_t* vp, const i128* vx,
+                                                 int hull_first, i128 base, int64_t& pt, i128& X) {
+    int lo = 0, hi = np - 1;   // the last piece whose first rank is <= r
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (c[mid].cum <= r) lo = mid; else hi = mid - 1;
+    }
+    ws_piece_vertex(c[lo], c[lo].lo + (r - c[lo].cum), vp, vx, hull_first, base, pt, X);
+}
+__device__ __forceinline__ int ws_cached_find(const Piece* c, int np, int r) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (c[mid].cum <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The bridge of two node hulls searched by the whole CTA, for merges whose
+// bridge lies beyond the prefetched window (typically near the root, where
+// one side loses thousands of vertices).  Same definitions as ws_bridge:
+// right(i, j) = R_{j+1} on or below the line (L_i, R_j); tangent(i) = the
+// first j with !right(i, j) (right(i, .) is true then false along the convex
+// chain R); survives(i) = i == 0 or L_{i-1}, L_i, R_tangent(i) convex
+// (survivors are a prefix of L); istar = the last survivor below the
+// junction, jstar = tangent(istar).  Each round of the outer search gives
+// one candidate i to each warp; a warp finds tangent(i) by a 32-way search
+// (every lane tests one j), so a merge costs about log_9(p) * log_33(q)
+// rounds instead of a serial gallop through global memory.  Requires the
+// junction not to be a vertex and both hulls to have >= 2 vertices.  The
+// piece lists are copied into `cache` (capacity >= npL + npR).  All threads
+// call it; it ends synchronised with m.is/js/pl/pr set and m.ok = 1.
+__device__ void ws_parallel_bridge(Piece* cache, MergeSmem& m, const Piece* PL, const Piece* PR, const uint16_t* vp,
+                                   const i128* vx, int hull_first, const SegConst& sc) {
+    constexpr int NW = HNT / 32;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int npL = m.npL, npR = m.npR;
+    Piece* cL = cache;
+    Piece* cR = cache + npL;
+    for (int k = t; k < npL + npR; k += HNT) cache[k] = ws_ld_piece(k < npL ? PL + k : PR + (k - npL));
+    __syncthreads();
+    const int p = cL[npL - 1].cum + (cL[npL - 1].hi - cL[npL - 1].lo) - 1;   // L_p = R_0: the junction
+    const int q = cR[npR - 1].cum + (cR[npR - 1].hi - cR[npR - 1].lo) - 1;
+    const i128 baseR = m.totL;
+    if (p < 1 || q < 1) return;   // (not reached from the window walk) left to the serial search
+    if (t == 0) {   // the junction stays a vertex: keep all of L, drop R_0 (as ws_bridge's flag 0)
+        int64_t pa, pb, pc;
+        i128 Xa, Xb, Xc;
+        ws_cached_vertex(cL, npL, p - 1, vp, vx, hull_first, 0, pa, Xa);
+        ws_cached_vertex(cL, npL, p, vp, vx, hull_first, 0, pb, Xb);
+        ws_cached_vertex(cR, npR, 1, vp, vx, hull_first, baseR, pc, Xc);
+        m.cand_s[0] = ws_convex(Xa, Xb, Xc, pa, pb, pc, sc) ? 1 : 0;
+        if (m.cand_s[0]) {
+            m.is = p; m.js = 1;
+            m.pl = ws_cached_find(cL, npL, p);
+            m.pr = ws_cached_find(cR, npR, 1);
+            m.ok = 1;
+        }
+    }
+    __syncthreads();
+    const bool junction_vertex = m.cand_s[0] != 0;
+    __syncthreads();   // every thread has read the flag before the search reuses cand_s
+    if (junction_vertex) return;   // (m.ok set)
+    // first j in [0, q] with !right(i, j), by the whole warp
+    auto tangent = [&](int64_t pi, const i128& Xi) -> int {
+        int jl = -1, jh = q;   // right(i, jl) (or jl = -1), !right(i, jh) (jh = q: no R_{q+1})
+        while (jh - jl > 1) {
+            const int span = jh - jl - 1;   // candidates jl + 1 .. jh - 1
+            const int j = (span <= 32) ? jl + 1 + lane : jl + 1 + (int)(((long long)span * lane) >> 5);
+            const bool valid = j < jh;
+            bool rt = false;
+            if (valid) {
+                int64_t pj, pk;
+                i128 Xj, Xk;
+                ws_cached_vertex(cR, npR, j, vp, vx, hull_first, baseR, pj, Xj);
+                ws_cached_vertex(cR, npR, j + 1, vp, vx, hull_first, baseR, pk, Xk);
+                rt = !ws_convex(Xi, Xj, Xk, pi, pj, pk, sc);
+            }
+            const unsigned bt = __ballot_sync(WS_FULL_MASK, valid && rt);
+            const unsigned bf = __ballot_sync(WS_FULL_MASK, valid && !rt);
+            if (bt) jl = __shfl_sync(WS_FULL_MASK, j, 31 - __clz((int)bt));
+            if (bf) jh = __shfl_sync(WS_FULL_MASK, j, __ffs((int)bf) - 1);
+        }
+        return jh;
+    };
+    int good = 0, bad = p, jgood = -1;   // survives(good), !survives(bad) (bad = p: the junction)
+    while (bad - good > 1) {
+        const int span = bad - good - 1;
+        const int c = (span <= NW) ? good + 1 + w : good + 1 + (int)(((long long)span * w) / NW);
+        if (c < bad) {
+            int64_t pc;
+            i128 Xc;
+            ws_cached_vertex(cL, npL, c, vp, vx, hull_first, 0, pc, Xc);
+            const int jt = tangent(pc, Xc);
+            if (lane == 0) {
+                int64_t pm, pt;
+                i128 Xm, Xt;
+                ws_cached_vertex(cL, npL, c - 1, vp, vx, hull_first, 0, pm, Xm);
+                ws_cached_vertex(cR, npR, jt, vp, vx, hull_first, baseR, pt, Xt);
+                m.cand_i[w] = c;
+                m.cand_j[w] = jt;
+                m.cand_s[w] = ws_convex(Xm, Xc, Xt, pm, pc, pt, sc) ? 1 : 0;
+            }
+        } else if (lane == 0) {
+            m.cand_i[w] = -1;
+        }
+        __syncthreads();
+        int ng = good, nb = bad, nj = jgood;
+        for (int k = 0; k < NW; ++k) {
+            const int ci = m.cand_i[k];
+            if (ci < 0) continue;
+            if (m.cand_s[k]) { if (ci > ng) { ng = ci; nj = m.cand_j[k]; } }
+            else if (ci < nb) nb = ci;
+        }
+        good = ng; bad = nb; jgood = nj;
+        __syncthreads();
+    }
+    if (jgood < 0 && w == 0) {   // istar = 0 was never a candidate: its tangent
+        int64_t p0;
+        i128 X0;
+        ws_cached_vertex(cL, npL, 0, vp, vx, hull_first, 0, p0, X0);
+        const int jt = tangent(p0, X0);
+        if (lane == 0) m.cand_j[0] = jt;
+    }
+    __syncthreads();
+    if (t == 0) {
+        const int js = jgood >= 0 ? jgood : m.cand_j[0];
+        m.is = good;
+        m.js = js;
+        m.pl = ws_cached_find(cL, npL, good);
+        m.pr = js <= q ? ws_cached_find(cR, npR, js) : npR;
+        m.ok = 1;
+    }
+    __syncthreads();
+}
 
 // Merge the node hulls whose piece lists start at Lg and Rg (global hull-tile
 // indices, Rg > Lg adjacent); the result replaces the list at Lg.  All
@@ -161,7 +299,8 @@ struct MergeSmem {
 // walks them in shared memory and falls back to the global search only if
 // the bridge leaves that window.
 __device__ __noinline__ void ws_merge_children(MergeSmem& m, Piece* pieces, int32_t* npieces, i128* ntotal, int Lg, int Rg,
-                                  const uint16_t* vp, const i128* vx, int hull_first, const SegConst& sc) {
+                                  const uint16_t* vp, const i128* vx, int hull_first, const SegConst& sc,
+                                  Piece* cache, int cache_cap) {
     const int t = threadIdx.x;
     Piece* PL = pieces + Lg;
     Piece* PR = pieces + Rg;
@@ -258,6 +397,9 @@ __device__ __noinline__ void ws_merge_children(MergeSmem& m, Piece* pieces, int3
         __syncwarp();
     }
     __syncthreads();
+    // the bridge reaches beyond the window: the CTA searches it in parallel
+    // (the serial walk and gallop below remain for lists too long to cache)
+    if (!m.ok && m.npL + m.npR <= cache_cap) ws_parallel_bridge(cache, m, PL, PR, vp, vx, hull_first, sc);
     if (t == 0) {
         const int npL = m.npL, npR = m.npR;
         const i128 totL = m.totL;
@@ -455,8 +597,10 @@ __global__ void __launch_bounds__(HNT, 3) k_tile_hull(const typename KeyOf<T>::K
         }
         __syncthreads();
         if (!s.go) break;
+        // the tile's prefix sums are dead during the climb: they cache piece lists
         ws_merge_children(s.ms, pieces, npieces, tile_total, ls.hull_first + parent_base, ls.hull_first + right_base,
-                          vp, vx, ls.hull_first, s.sc);
+                          vp, vx, ls.hull_first, s.sc, reinterpret_cast<Piece*>(&s.pre),
+                          (int)(sizeof(s.pre) / sizeof(Piece)));
     }
 }
 
