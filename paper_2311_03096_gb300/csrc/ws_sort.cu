@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(WS_SORT_NT, 2) k_onesweep(const T* __restrict_
     // lane l being key w*32*ITEMS + 32k + l, so ranking items in order k and
     // lanes in order l is stable.
     K key[ITEMS];
-    int pos[ITEMS];
+    static_assert(ITEMS % 2 == 0 && TILE <= 65536, "ranks are packed two per word");
+    uint32_t pos2[ITEMS / 2];   // warp-local rank of item k in half k % 2 of word k / 2 (fewer registers)
     const int base = w * 32 * ITEMS + lane;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
@@ -144,7 +145,8 @@ __global__ void __launch_bounds__(WS_SORT_NT, 2) k_onesweep(const T* __restrict_
         const int before = v ? (int)my[dg] : 0;
         __syncwarp();
         const int r = __popc(peers & lt);
-        pos[k] = before + r;
+        const uint32_t rk = (uint32_t)(before + r);
+        if (k % 2 == 0) pos2[k / 2] = rk; else pos2[k / 2] |= rk << 16;
         if (v && r == 0) { my[dg] = (uint32_t)(before + __popc(peers)); mb[dg] = 0u; }
         __syncwarp();
     }
@@ -174,7 +176,8 @@ __global__ void __launch_bounds__(WS_SORT_NT, 2) k_onesweep(const T* __restrict_
     for (int k = 0; k < ITEMS; ++k) {
         if (base + k * 32 < td.len) {
             const uint32_t dg = (uint32_t)(key[k] >> shift) & 0xffu;
-            skeys[pos[k] + (int)(dstart[dg] + my[dg])] = key[k];
+            const int rk = (int)((pos2[k / 2] >> (16 * (k % 2))) & 0xffffu);
+            skeys[rk + (int)(dstart[dg] + my[dg])] = key[k];
         }
     }
 
