@@ -52,13 +52,29 @@ __global__ void __launch_bounds__(WS_SORT_NT) k_hist(const T* __restrict__ value
     const TileDesc td = tiles[blockIdx.x];
     bool bad = false;
     int emin = 0x7fffffff;
-    for (int i = threadIdx.x; i < td.len; i += WS_SORT_NT) {
-        T v = values[td.vpos + i];
+    auto count = [&](T v) {
         bad |= !ws_isfinite(v);
         if (v != (T)0) emin = min(emin, ws_eff_exp(v));
-        typename KO::K k = KO::to_key(v);
+        const typename KO::K k = KO::to_key(v);
 #pragma unroll
         for (int p = 0; p < P; ++p) atomicAdd(&h[p * 256 + (int)((k >> (8 * p)) & 0xff)], 1u);
+    };
+    const T* src = values + td.vpos;
+    constexpr int VEC = 16 / (int)sizeof(T);                  // values per 16-byte load
+    constexpr int NV = WS_SORT_TILE / (WS_SORT_NT * VEC);     // 16-byte loads per thread
+    if (td.len == WS_SORT_TILE && (((uintptr_t)src) & 15) == 0) {
+        // whole, aligned tile: every load issued before the first count
+        uint4 buf[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) buf[j] = __ldcs(reinterpret_cast<const uint4*>(src) + j * WS_SORT_NT + threadIdx.x);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const T* e = reinterpret_cast<const T*>(&buf[j]);
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) count(e[u]);
+        }
+    } else {
+        for (int i = threadIdx.x; i < td.len; i += WS_SORT_NT) count(src[i]);
     }
     if (bad) ws_flag(status, WS_STATUS_NONFINITE);
 #pragma unroll
