@@ -165,6 +165,56 @@ def dlambda(grad_out, ids, offsets=None):
     return res
 
 
+def imminent_collisions_v2(w, lam: float, max_rounds: int | None = None):
+    """The paper's Imminent Collisions algorithm, version 2 (the appendix's
+    Algorithm "Imminent collisions algorithm (v2)"; Sec. 4.1 for IC), in FP64
+    numpy, kept here to count its rounds.
+
+    Particles are the sorted weights x_k with velocity v_k = lam (d + 1 - 2k)/(d - 1)
+    and mass 1.  One round marks a new block wherever the destination y = x + v
+    strictly increases from one particle to the next, so every maximal run of
+    non-increasing y collides at once (a prefix sum numbers the blocks; positions
+    and velocities are mass-weighted means).  Rounds repeat until one changes
+    nothing; that last round is counted, as in the algorithm's repeat-until.
+
+    Returns (out, ids, n_clusters, rounds, converged); out/ids are in input order
+    (ids rank the blocks from the left).  With max_rounds the loop stops early and
+    converged is False if the last round still merged."""
+    perm, xs = sort(w)
+    d = xs.shape[0]
+    if d == 0:
+        return np.empty(0), np.empty(0, np.int32), 0, 0, True
+    k = np.arange(1, d + 1, dtype=np.float64)
+    v = lam * (d + 1 - 2 * k) / (d - 1) if d > 1 else np.zeros(1)
+    x = xs.copy()
+    m = np.ones(d)
+    starts = np.arange(d)          # first sorted position of every block
+    rounds, converged = 0, False
+    while max_rounds is None or rounds < max_rounds:
+        n = x.shape[0]
+        y = x + v
+        c = np.zeros(n, np.int64)
+        c[1:] = y[:-1] < y[1:]
+        i = np.cumsum(c)
+        rounds += 1
+        if i[-1] + 1 == n:
+            converged = True
+            break
+        mn = np.bincount(i, weights=m)
+        x = np.bincount(i, weights=x * m) / mn
+        v = np.bincount(i, weights=v * m) / mn
+        m = mn
+        starts = starts[np.concatenate([[True], c[1:] != 0])]
+    sizes = np.diff(np.concatenate([starts, [d]]))
+    ids_sorted = np.repeat(np.arange(starts.shape[0], dtype=np.int32), sizes)
+    vals_sorted = np.repeat(x + v, sizes)
+    ids = np.empty(d, np.int32)
+    out = np.empty(d, np.float64)
+    ids[perm] = ids_sorted
+    out[perm] = vals_sorted
+    return out, ids, int(starts.shape[0]), rounds, converged
+
+
 def ws_measure(w) -> float:
     """Weight-sharing measure of the CIFAR10 experiment: #distinct nonzero weights /
     #nonzero weights (0 when every weight is zero); -0.0 counts as zero."""

@@ -277,6 +277,48 @@ def test_tie_lattice_matches_integer_pav(d, binade):
     np.testing.assert_array_equal(out, (1.0 if binade else 0.0) + means * 2.0 ** -24)
 
 
+@pytest.mark.parametrize("lam", [0.0, 1e-2, 0.3, 1.0, 100.0])
+def test_ic_v2_converges_to_the_prox_partition(lam):
+    # IC v2 (appendix algorithm) only performs collisions that happen, and stops
+    # when no destination order is violated: its blocks are the prox clusters
+    w = inputs.normal_with_duplicates(5000, seed=11)
+    out, ids, nc, rounds, conv = oracle.imminent_collisions_v2(w, lam)
+    pout, pids, pnc = oracle.prox(w, lam)
+    assert conv and nc == pnc and np.array_equal(ids, pids)
+    np.testing.assert_allclose(out, pout, atol=1e-12 * (np.abs(w).max() + lam))
+
+
+def test_ic_v2_on_tie_lattice_is_exact():
+    from parity import lattice_expected
+    w, lam, n = inputs.tie_lattice(4096, seed=8)
+    ids_ref, _, nc_ref = lattice_expected(n, 4096)
+    _, ids, nc, _, conv = oracle.imminent_collisions_v2(w, lam)
+    assert conv and nc == nc_ref and np.array_equal(ids, ids_ref)
+
+
+@pytest.mark.parametrize("d", [16, 1024, 4096])
+def test_ic_v2_round_counts(d):
+    # Sec. 4.1: on the cascade the right half joins one particle per round, d/2
+    # rounds; plus the round that pools the left half and the final round that
+    # changes nothing.  The mirror pools every pair in one round.
+    w, lam = inputs.cascade(d, seed=1)
+    _, _, nc, rounds, conv = oracle.imminent_collisions_v2(w, lam)
+    assert conv and nc == 1 and rounds == d // 2 + 2
+    w, lam = inputs.mirror(d, seed=2, shuffle=True)
+    _, _, nc, rounds, conv = oracle.imminent_collisions_v2(w, lam)
+    assert conv and nc == d // 2 and rounds == 2
+
+
+def test_ic_v2_round_cap_gives_a_refinement():
+    # stopped early, every block still lies inside one prox cluster
+    w, lam = inputs.cascade(1024, seed=1, shuffle=True)
+    _, ids, nc, rounds, conv = oracle.imminent_collisions_v2(w, lam, max_rounds=20)
+    assert rounds == 20 and not conv and nc > 1
+    _, pids, _ = oracle.prox(w, lam)
+    for b in np.unique(ids):
+        assert np.unique(pids[ids == b]).shape[0] == 1
+
+
 def test_backward_is_cluster_average_and_matches_fd():
     rng = np.random.default_rng(4)
     d, lam, eps = 64, 0.05, 1e-6
