@@ -76,15 +76,6 @@ struct TilePrefix {
 // Representation of a tile's prefix sums.
 enum { WS_TILE_WIDE = 0, WS_TILE_NARROW = 1, WS_TILE_BINADE = 2 };
 
-// kr[i] = key of sorted element first + i (first = threadIdx.x * M); k0, kn =
-// keys of elements 0 and n - 1.  Modes:
-//   BINADE: all keys share sign and exponent, so key - k0 is the value
-//           difference in ulps of that binade, exactly; s64 holds prefix sums
-//           of (key - k0) in ulp units; one ulp = 2^sh global fixed-point units
-//           (sh >= 0 is required: otherwise the global image truncates).
-//   NARROW: s64 holds D_p = sum (q_j - q_0) in global units.
-//   WIDE:   s64 holds chunk-relative prefixes, base[] the chunk starts (128-bit).
-// q0_out = global fixed-point image of element 0; total_out = X_n (global).
 // Is a tile with first/last keys k0, kn (n elements) a BINADE tile, and the
 // binade's shift sh against the segment scale (see ws_tile_prefix)?
 template <typename T>
@@ -96,6 +87,15 @@ __device__ __forceinline__ bool ws_tile_binade(typename KeyOf<T>::K k0, typename
     return same_binade && (uint64_t)(kn - k0) <= ((uint64_t)1 << 62) / (uint64_t)n;
 }
 
+// kr[i] = key of sorted element first + i (first = threadIdx.x * M); k0, kn =
+// keys of elements 0 and n - 1.  Modes:
+//   BINADE: all keys share sign and exponent, so key - k0 is the value
+//           difference in ulps of that binade, exactly; s64 holds prefix sums
+//           of (key - k0) in ulp units; one ulp = 2^sh global fixed-point units
+//           (sh >= 0 is required: otherwise the global image truncates).
+//   NARROW: s64 holds D_p = sum (q_j - q_0) in global units.
+//   WIDE:   s64 holds chunk-relative prefixes, base[] the chunk starts (128-bit).
+// q0_out = global fixed-point image of element 0; total_out = X_n (global).
 // thr_dst/thr_val: an optional shared-memory store that is issued after the
 // prefix's first barrier (so it may overwrite storage that was read before
 // the call) and is visible to every thread on return.
