@@ -12,7 +12,10 @@
 // the process exits.  Host code cannot use the array's name as a device
 // address, so the address is looked up with cudaGetSymbolAddress once per
 // device, with that device current, the first time the entry point runs on
-// it; later calls reuse the cached address.
+// it; later calls reuse the cached address.  That first call on a device
+// should therefore come before any stream capture begins, and the cached
+// address does not survive a device reset (cudaDeviceReset): the entry point
+// must not be used across one.
 #include <mutex>
 
 #include "../../include/ws_prox.h"
@@ -91,8 +94,12 @@ ws_status run(const void* grad_out, const int32_t* ids, int64_t d, void* grad_in
     int32_t* cnt = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(scratch) + kSumBytes);
     const int nt = 256;
     const int nb = (int)((d + nt - 1) / nt < 4096 ? (d + nt - 1) / nt : 4096);
+    // each launch is checked on its own (the caller's stale errors were
+    // cleared on entry), so a failure is reported by the call that caused it
     k_na_clear<T><<<nb, nt, 0, st>>>(sum, cnt, d);
+    if (cudaGetLastError() != cudaSuccess) return WS_ERR_CUDA;
     k_na_accum<T><<<nb, nt, 0, st>>>((const T*)grad_out, ids, d, sum, cnt);
+    if (cudaGetLastError() != cudaSuccess) return WS_ERR_CUDA;
     k_na_apply<T><<<nb, nt, 0, st>>>(ids, d, sum, cnt, (T*)grad_in);
     if (cudaGetLastError() != cudaSuccess) return WS_ERR_CUDA;
     return WS_OK;
@@ -106,6 +113,7 @@ extern "C" ws_status ws_prox_backward_noalloc(const void* grad_out, const int32_
     if (dtype != WS_F32 && dtype != WS_F64) return WS_ERR_INVALID;
     if (d == 0) return WS_OK;
     if (!grad_out || !cluster_ids || !grad_in) return WS_ERR_INVALID;
+    cudaGetLastError();   // a launch error left by earlier, unrelated code is not this call's
     void* scratch = nullptr;
     ws_status s = scratch_for_current_device(&scratch);
     if (s != WS_OK) return s;
