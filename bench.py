@@ -44,6 +44,16 @@ ALGO_BYTES_PER_ELEM_F32 = {
     "lookup": 12,     # read w, write out and cluster id (I/O floor)
 }
 
+# Whole-step byte models per element (FP32 storage), fixed before tuning:
+# the I/O floor (read w, write out and cluster id), this library's key-only
+# sort pipeline (histogram read 4 + four 8-bit passes x (read + write key) 32 +
+# merge read of the sorted keys 4 + lookup 12) and the sort-with-index-payload
+# pipeline of the design survey (80 B).  One-CTA segments of a batch move the
+# I/O floor only.
+IO_FLOOR_B = 12
+ONE_CTA_MAX_F32 = 4096   # FP32 segments up to this length run one CTA each
+MODEL_B = {"key_only_52B": 52, "index_payload_80B": 80}
+
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture, and the hash of the kernel sources it was taken on; reported as
 # null once the sources change.  tile_hull: captured at d = 2^24 (lambda = 1),
@@ -70,6 +80,36 @@ def load_peaks():
             j = json.load(f)
         return float(j["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def cpu_model() -> str:
+    """Host CPU model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def byte_fracs(elems_small: int, elems_large: int, ms: float, peak_gbs: float) -> dict:
+    """Fractions of the measured HBM peak that the byte models above reach in `ms`."""
+    def frac(b_large, b_small):
+        return (b_large * elems_large + b_small * elems_small) / (ms / 1e3) / (peak_gbs * 1e9)
+
+    return {"model_bytes_frac": {k: frac(b, IO_FLOOR_B) for k, b in MODEL_B.items()},
+            "io_floor_frac": frac(IO_FLOOR_B, IO_FLOOR_B)}
 
 
 def dist_env():
@@ -172,7 +212,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": cfg,
-        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "cpu_model": cpu_model(), "kind": "oracle",
                          "sample": f"first {n} elements of the workload vector per step (lambda cycling)"},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -203,7 +243,7 @@ def _oracle_segments(args):
     return int(off[-1])
 
 
-def bench_batched(ws, ctx, stream, reps=5):
+def bench_batched(ws, ctx, stream, peak, reps=5):
     """Batched MLP layout (rows, whole layers, 4096 log-uniform extras): elements/s
     of each set and of all of them in one call (eager and CUDA-graph replay),
     errors against the oracle on sampled segments, and the oracle run
@@ -234,8 +274,11 @@ def bench_batched(ws, ctx, stream, reps=5):
         nc = torch.zeros(len(idx), dtype=torch.int64, device=dev)
         run = lambda: plan.forward(v, lt, "fp32comp", out=out, id_out=ids, n_clusters=nc, stream=stream)  # noqa: E731
         ms = _time_calls(run, stream, reps)
+        e_small = int(lens[lens <= ONE_CTA_MAX_F32].sum())
+        e_large = int(sub_off[-1]) - e_small
         entry = {"elements": int(sub_off[-1]), "segments": int(len(idx)), "ms": ms,
-                 "elements_per_s": sub_off[-1] / (ms / 1e3)}
+                 "elements_per_s": sub_off[-1] / (ms / 1e3), "elements_one_cta": e_small,
+                 **byte_fracs(e_small, e_large, ms, peak)}
         if name == "all":
             g = torch.cuda.CUDAGraph()
             side = torch.cuda.Stream()
@@ -250,6 +293,7 @@ def bench_batched(ws, ctx, stream, reps=5):
             msg = _time_calls(g.replay, stream, reps)
             entry["graph_ms"] = msg
             entry["graph_elements_per_s"] = sub_off[-1] / (msg / 1e3)
+            entry["graph"] = byte_fracs(e_small, e_large, msg, peak)
             tuned = ws.Plan.autotuned(sub_off, v, lt, "fp32comp", thresholds=[0, 1024, 2048, 4096], reps=2, ctx=ctx)
             entry["autotune"] = {"threshold": tuned.threshold,
                                  "ms_by_threshold": dict(zip(["0", "1024", "2048", "4096"], tuned.times_ms))}
@@ -290,9 +334,44 @@ def bench_batched(ws, ctx, stream, reps=5):
     with mp.get_context("spawn").Pool(len(tasks)) as pool:
         n = sum(pool.map(_oracle_segments, tasks))
     dt = time.time() - t0
-    res["oracle_parallel"] = {"value": n / dt, "unit": "elements/s", "cores": len(tasks), "kind": "oracle",
+    res["oracle_parallel"] = {"value": n / dt, "unit": "elements/s", "cores": len(tasks), "cpu_model": cpu_model(),
+                              "kind": "oracle",
                               "sample": f"{len(take)} segments (all rows, all layers, 256 extras; {n} elements), "
                                         f"{dt:.1f} s including process start"}
+    return res
+
+
+def bench_configs(ws, ctx, stream):
+    """Timings of the other single-vector configurations: d = 4096 FP64 N(0,1)
+    (lambda in {0, 0.1, 1, 1000}, FP64 arithmetic) and the adversarial cascade
+    and mirror at d = 2^24 (sorted and shuffled)."""
+    import torch
+
+    from paper_2311_03096_gb300 import inputs
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    res = {}
+    w = torch.from_numpy(inputs.normal(4096, seed=0, dtype=np.float64)).to(dev)
+    out = torch.empty_like(w)
+    ids = torch.empty(4096, dtype=torch.int32, device=dev)
+    nc = torch.zeros(1, dtype=torch.int64, device=dev)
+    for lam in (0.0, 0.1, 1.0, 1000.0):
+        run = lambda: ws.prox(w, lam, "fp64", ctx=ctx, out=out, id_out=ids, n_clusters=nc, stream=stream)  # noqa
+        ms = _time_calls(run, stream, 200)
+        res[f"d4096_f64_lam{lam:g}"] = {"us_per_call": 1e3 * ms, "elements_per_s": 4096 / (ms / 1e3),
+                                        "clusters": int(nc.item())}
+    d = 1 << 24
+    for name, gen in (("cascade", inputs.cascade), ("mirror", inputs.mirror)):
+        for shuffle in (False, True):
+            w_np, lam = gen(d, seed=0, shuffle=shuffle)
+            w = torch.from_numpy(w_np).to(dev)
+            out = torch.empty_like(w)
+            ids = torch.empty(d, dtype=torch.int32, device=dev)
+            run = lambda: ws.prox(w, lam, "fp32comp", ctx=ctx, out=out, id_out=ids, n_clusters=nc, stream=stream)  # noqa
+            ms = _time_calls(run, stream, 10)
+            res[f"{name}_2^24_{'shuffled' if shuffle else 'sorted'}"] = {
+                "ms": ms, "elements_per_s": d / (ms / 1e3), "clusters": int(nc.item()), "merges": d - int(nc.item())}
+    ctx.check(what="bench configs")
     return res
 
 
@@ -384,8 +463,7 @@ def main():
     torch.cuda.synchronize()
     ctx.check(what="bench warm-up")
 
-    # ---- timed region: K steps, inputs resident in HBM
-    ctx.profile(True)
+    # ---- timed region: K steps, inputs resident in HBM, no per-kernel events
     launches0 = ctx.launch_count()
     replicas.barrier()
     torch.cuda.synchronize()
@@ -401,16 +479,31 @@ def main():
     replicas.barrier()
     launches = ctx.launch_count() - launches0
     ms_total = e0.elapsed_time(e1)
-    kern = ctx.profile_read()
-    ctx.profile(False)
     ctx.check(what="bench timed region")
     ms_max = replicas.max_over_ranks(ms_total, dev)
     value = replicas.job_rate(args.d * args.steps, world, ms_max)
     ms_per_step = ms_max / args.steps
 
+    # ---- kernel timing: the same steps again with a CUDA event pair recorded
+    # around every launch on the launching stream (kept out of the value above)
+    ctx.profile(True)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for k in range(args.steps):
+        ws.prox(w, LAMBDAS[k % 3], args.prec, ctx=ctx, out=out, n_clusters=nc)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = p0.elapsed_time(p1)
+    kern = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check(what="bench kernel timing")
+
     # ---- dominant kernel roofline (live CUDA-event durations from the timed region)
     peak, peak_kind = load_peaks()
-    shares = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / ms_total} for k, v in kern.items()}
+    shares = {k: {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / v[1], "share": v[0] / ms_prof}
+              for k, v in kern.items()}
     dom = max(kern.items(), key=lambda kv: kv[1][0])[0] if kern else None
     roofline = None
     if dom is not None:
@@ -421,7 +514,10 @@ def main():
             achieved = per_launch * args.d / (ms_avg / 1e3) / 1e9
             roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
-                        "bytes_per_launch": per_launch * args.d, "ms_per_launch": ms_avg, "traffic": traffic}
+                        "bytes_per_launch": per_launch * args.d, "ms_per_launch": ms_avg, "traffic": traffic,
+                        "timing": "CUDA events around every launch on the launching stream, in a second run "
+                                  "of the timed loop (same steps and inputs; the value comes from the first, "
+                                  "unprofiled run)"}
         else:
             roofline = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
                         "ms_per_launch": ms_avg, "traffic": traffic}
@@ -533,7 +629,8 @@ def main():
                 same = bool(np.array_equal(i.cpu().numpy(), ref_ids))
                 errs[f"{prec}_lam{lam:g}"] = {"max_err_rel_to_max_w_plus_lambda": err, "partition_equal": same}
         variants["error_vs_oracle_2^20"] = errs
-        variants["batched_mlp"] = bench_batched(ws, ctx, stream)
+        variants["batched_mlp"] = bench_batched(ws, ctx, stream, peak)
+        variants["configs"] = bench_configs(ws, ctx, stream)
         variants["train_step"] = bench_train(ws, ctx, stream)
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample
@@ -544,15 +641,16 @@ def main():
         oracle.build()
         n = 1 << 22
         rate, dt = oracle_rate(w_np[:n], 6)
-        cpu = {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": "elements/s", "cores": 1, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"first {n} elements of the workload vector, 6 calls cycling lambda ({dt:.1f} s)"}
 
+    fracs = byte_fracs(0, args.d, ms_per_step, peak)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.prec == "fp32comp" else "f64", "data": "synthetic",
-            "config": config_dict(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": config_dict(args, world), "roofline": roofline, **fracs, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "kernels": shares, "variants": variants,
         }
         print(json.dumps(line), flush=True)
