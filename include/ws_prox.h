@@ -35,6 +35,17 @@
  *     nothing is enqueued.  Errors found on the device (a NaN/Inf input, a
  *     bounded wait that gave up) are OR-ed into the context's status word and
  *     reported by ws_get_status; outputs of that call are then unspecified.
+ *   - Concurrency: a plan's scratch (sort buffers, look-back words, hull and
+ *     cluster tables) is reused by every call made with that plan.  The
+ *     single-vector calls (ws_prox, ws_prox_l1, ws_prox_backward,
+ *     ws_prox_dlambda, ws_R) share one plan per (d, dtype) cached in the
+ *     context.  So calls that use the same plan -- or the same context with
+ *     the same single-vector shape -- must be ordered on one stream (or be
+ *     otherwise serialised); if their kernels overlap on the GPU their
+ *     results are undefined.  Calls on different plans, or on different
+ *     contexts, may run concurrently on different streams.  A context and its
+ *     plans may be used from several host threads only if the caller
+ *     serialises those calls.
  */
 #ifndef WS_PROX_H
 #define WS_PROX_H
@@ -206,6 +217,23 @@ void ws_debug_set_spin_limit(ws_ctx* ctx, int64_t limit);
  * Test hook: lets small inputs exercise the device-wide path. */
 void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max);
 
+/* Round cap of the Imminent Collisions rounds that every hull tile of the
+ * device-wide path runs first (appendix algorithm "Imminent collisions
+ * algorithm (v2)"); a tile whose rounds have not converged within the cap
+ * takes the tree of bridge merges instead.  0 skips the rounds (every tile
+ * takes the merges); a negative value restores the default (24).  Takes
+ * effect on the next call.  Test and benchmark hook. */
+void ws_debug_set_ic_cap(ws_ctx* ctx, int cap);
+
+/* How the hull tiles of the last ws_prox call for (d, dtype) on this context
+ * were built.  counts (HOST, n_counts >= 3 int64, overwritten):
+ * counts[0] = tiles built by the general kernel, counts[1] = tiles whose
+ * rounds hit the cap (tree of merges), counts[r + 1] = tiles whose rounds
+ * converged after r rounds (the last, unchanged round included; r >=
+ * n_counts - 1 is counted in the last slot).  Synchronises the device.
+ * All zero if no such call was made.  Benchmark hook. */
+ws_status ws_debug_hull_stats(ws_ctx* ctx, int64_t d, ws_dtype dtype, int64_t* counts, int n_counts);
+
 /* Runs only the radix sort of the device-wide path and writes, for every
  * segment that the plan sends down that path, its values sorted ascending in
  * IEEE total order (-0 before +0) at the segment's own position in
@@ -230,7 +258,15 @@ ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, voi
  *     (d elements of dtype, d int32, d elements of dtype); grad_in may alias
  *     grad_out.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current.  No call allocates.
+ *     (cudaGetSymbolAddress) with that device current and caches it; make
+ *     that first call before any stream capture begins.  The cached address
+ *     does not survive cudaDeviceReset: do not use the entry point across a
+ *     device reset.  No call allocates.
+ *   - The device that is current when the call is made must be the device
+ *     that holds grad_out, cluster_ids and grad_in, and `stream` must belong
+ *     to it.
+ *   - A launch error left pending by earlier, unrelated code is cleared on
+ *     entry; WS_ERR_CUDA reports only this call's own launch failures.
  *   - d > WS_NOALLOC_MAX_ELEMS or d < 0 returns WS_ERR_INVALID and enqueues
  *     nothing; d == 0 is a no-op.  Ids outside [0, d) are skipped and leave
  *     their grad_in entry unchanged.

@@ -28,6 +28,7 @@ struct ws_ctx {
     uint32_t* status = nullptr;   // device status word
     uint64_t spin_limit = WS_DEFAULT_SPIN;
     int64_t small_max_override = -1;
+    int ic_cap = 24;   // in-tile Imminent Collisions round cap
     std::vector<PlanCacheEntry> cache;
     std::mutex mu;
     WsProf prof;
@@ -70,6 +71,16 @@ struct ws_plan {
     Piece* pieces = nullptr;
     int32_t* npieces = nullptr;
     int32_t* tile_piece = nullptr;
+    int32_t* tile_general = nullptr;
+    int32_t* keepR = nullptr;
+    int32_t* keepL = nullptr;
+    int32_t* jflag0 = nullptr;
+    int32_t* seg_mode = nullptr;
+    i128* tile_base = nullptr;
+    TileScale* scales = nullptr;
+    int32_t* tile_rounds = nullptr;
+    i128* seg_total = nullptr;
+    int32_t* seg_below = nullptr;
     SegRuntime* rt = nullptr;
     void* table = nullptr;
     DirEntry* dir = nullptr;
@@ -106,6 +117,17 @@ LargeWork<T> make_work(const ws_plan* p) {
     W.pieces = p->pieces;
     W.npieces = p->npieces;
     W.tile_piece = p->tile_piece;
+    W.tile_general = p->tile_general;
+    W.keepR = p->keepR;
+    W.keepL = p->keepL;
+    W.jflag0 = p->jflag0;
+    W.seg_mode = p->seg_mode;
+    W.tile_base = p->tile_base;
+    W.scales = p->scales;
+    W.tile_rounds = p->tile_rounds;
+    W.ic_cap = p->ctx->ic_cap;
+    W.seg_total = p->seg_total;
+    W.seg_below = p->seg_below;
     W.rt = p->rt;
     W.table = (CEntry<T>*)p->table;
     W.dir = p->dir;
@@ -221,6 +243,16 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->pieces, sizeof(Piece) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->npieces, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->tile_piece, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->tile_general, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->keepR, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->keepL, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->jflag0, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->seg_mode, sizeof(int32_t) * p->n_lseg))) return st;
+    if ((st = plan_alloc(p, (void**)&p->tile_base, sizeof(i128) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->scales, sizeof(TileScale) * WS_NSCALE * p->n_lseg))) return st;
+    if ((st = plan_alloc(p, (void**)&p->tile_rounds, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->seg_total, sizeof(i128) * p->n_lseg))) return st;
+    if ((st = plan_alloc(p, (void**)&p->seg_below, sizeof(int32_t) * p->n_lseg))) return st;
     if ((st = plan_alloc(p, (void**)&p->rt, sizeof(SegRuntime) * p->n_lseg))) return st;
     // (+4 entries: the lookup reads whole 32-byte sectors of the table)
     if ((st = plan_alloc(p, &p->table, (f64 ? sizeof(CEntry<double>) : sizeof(CEntry<float>)) * (slots + 4)))) return st;
@@ -583,6 +615,35 @@ void ws_debug_set_spin_limit(ws_ctx* ctx, int64_t limit) {
     if (ctx) ctx->spin_limit = limit > 0 ? (uint64_t)limit : WS_DEFAULT_SPIN;
 }
 
+void ws_debug_set_ic_cap(ws_ctx* ctx, int cap) {
+    if (!ctx) return;
+    ctx->ic_cap = cap < 0 ? 24 : cap;
+}
+
+ws_status ws_debug_hull_stats(ws_ctx* ctx, int64_t d, ws_dtype dtype, int64_t* counts, int n_counts) {
+    if (!ctx || !counts || n_counts < 3 || d < 0) return WS_ERR_INVALID;
+    ws_plan* p = nullptr;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        for (auto& c : ctx->cache)
+            if (c.d == d && c.dtype == dtype && c.sort_only == 0) p = c.plan;
+    }
+    for (int i = 0; i < n_counts; ++i) counts[i] = 0;
+    if (!p || p->n_hull_tiles == 0) return WS_OK;
+    std::vector<int32_t> r((size_t)p->n_hull_tiles);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(r.data(), p->tile_rounds, sizeof(int32_t) * r.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return WS_ERR_CUDA;
+    }
+    for (int32_t v : r) {
+        if (v == -2) ++counts[0];
+        else if (v == -1) ++counts[1];
+        else ++counts[v + 1 < n_counts ? v + 1 : n_counts - 1];
+    }
+    return WS_OK;
+}
+
 void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max) {
     if (!ctx) return;
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -611,7 +672,8 @@ ws_status ws_debug_sort(ws_plan* plan, const void* values, void* sorted_out, voi
 }
 
 static const char* const kKernelNames[WSK_COUNT] = {"small", "hist", "hist_scan", "onesweep", "tile_hull",
-                                                     "root", "table", "big_gaps", "lookup", "backward", "misc"};
+                                                     "root", "table", "big_gaps", "lookup", "backward", "misc",
+                                                     "tile_general", "junction", "climb"};
 
 const char* ws_debug_kernel_name(int kind) {
     return (kind >= 0 && kind < WSK_COUNT) ? kKernelNames[kind] : nullptr;

@@ -11,7 +11,7 @@ template <> struct SmallCfg<double> { static constexpr int M = 8; static constex
 // around every kernel) and a launch counter.  Host-side only.
 enum WsKernelKind {
     WSK_SMALL = 0, WSK_HIST, WSK_HIST_SCAN, WSK_ONESWEEP, WSK_TILE_HULL, WSK_ROOT,
-    WSK_TABLE, WSK_BIG_GAPS, WSK_LOOKUP, WSK_BWD, WSK_MISC, WSK_COUNT
+    WSK_TABLE, WSK_BIG_GAPS, WSK_LOOKUP, WSK_BWD, WSK_MISC, WSK_TILE_GENERAL, WSK_JUNCTION, WSK_CLIMB, WSK_COUNT
 };
 struct WsProf {
     bool enabled = false;
@@ -91,6 +91,22 @@ struct DirEntry {
 };
 constexpr int WS_DIR_MAX_LOG2 = 22;   // <= 2^22 buckets per segment (32 MiB: stays in L2)
 
+// Constants of the exact hull test at one fixed-point unit scale of a
+// segment: the units of a one-binade hull tile (ulps of its binade) or the
+// segment's own scale.  Computed once per segment (k_scales) so that tiles do
+// no FP64 or wide-integer set-up work.
+struct TileScale {
+    SegConst sc;      // hull-test constants at this scale
+    float muq;        // lambda 2^L / (d - 1) in units, for the FP32 filter
+    int fast;         // muq usable by the filter
+    uint64_t modd;    // odd part of lambda 2^L (0 when lambda = 0) and its exponent
+    int sodd;
+    int pad;
+    int64_t t11;      // floor(2 lambda 2^L / (d - 1)), saturated at 2^62: two adjacent
+                      // elements collide at once (IC round 1) iff their gap <= t11 units
+};
+constexpr int WS_NSCALE = 64;   // per segment: binade shifts 0 .. FIX_OFS, then the segment scale last
+
 // Per-segment run-time values computed on the device.
 struct SegRuntime {
     int64_t n_clusters;
@@ -133,6 +149,17 @@ struct LargeWork {
     Piece* pieces;           // [n_hull_tiles]
     int32_t* npieces;        // [n_hull_tiles] pieces of the node whose first tile is this index
     int32_t* tile_piece;     // [n_hull_tiles] piece index in the root list or -1
+    int32_t* tile_general;   // [n_hull_tiles] 1: the tile's hull comes from the general kernel
+    int32_t* keepR;          // [n_hull_tiles] junction results (ws_tile.cu)
+    int32_t* keepL;          // [n_hull_tiles]
+    int32_t* jflag0;         // [n_hull_tiles]
+    int32_t* seg_mode;       // [n_lseg] 0: junctions resolved, 1: one cluster, 2: tree of merges
+    i128* tile_base;         // [n_hull_tiles] X at every hull tile's first point (segment frame)
+    TileScale* scales;       // [n_lseg][WS_NSCALE]
+    int32_t* tile_rounds;    // [n_hull_tiles] in-tile IC rounds to converge, -1 chain + trees, -2 general kernel
+    int ic_cap;              // in-tile IC round cap (0: chain + trees only)
+    i128* seg_total;         // [n_lseg] X of the whole segment
+    int32_t* seg_below;      // [n_lseg] a tile-hull vertex lies below the segment's chord
     SegRuntime* rt;          // [n_lseg]
     CEntry<T>* table;        // [n_keys + n_lseg]
     DirEntry* dir;           // directory slices
@@ -145,6 +172,12 @@ struct LargeWork {
 template <typename T>
 cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* status, uint64_t spin_limit,
                           cudaStream_t st, typename KeyOf<T>::K** sorted);
+// Lean tile hulls and the junction resolution (ws_tile.cu).
+template <typename T>
+cudaError_t ws_large_hull_fast(const LargeWork<T>& W, const typename KeyOf<T>::K* sorted, const double* lambdas,
+                               uint32_t* status, cudaStream_t st);
+template <typename T>
+cudaError_t ws_large_junctions(const LargeWork<T>& W, const double* lambdas, cudaStream_t st);
 template <typename T>
 cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* lambdas, T* out, int32_t* ids,
                           int64_t* n_clusters, int fp64, const WsEpi& ep, uint32_t* status, uint64_t spin_limit,

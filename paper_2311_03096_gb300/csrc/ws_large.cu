@@ -469,25 +469,23 @@ __device__ __noinline__ void ws_merge_children(MergeSmem& m, Piece* pieces, int3
 struct TileHullSmem {
     TilePrefix<HNT, HM> pre;
     HullSmem<HNT, HM> hull;
-    MergeSmem ms;
-    int go;
     SegConst sc;     // global fixed-point scale of the segment
     SegConst sct;    // scale of this tile when it lies in one binade
     float muq, muqt;
     int fast, fastt;
 };
 
-// Four CTAs per SM (64 registers; only the rare merge paths spill): much of the
-// kernel's time is spent at barriers while one thread searches a bridge, and a
-// fourth resident CTA hides more of it than the registers a third one would keep
-// (measured 3-10 % faster than three CTAs at 80 registers).
+// The general tile kernel: the exact hull of a tile whose prefix sums need
+// 128 bits (or whose bridge walks were too long for the lean kernel of
+// ws_tile.cu, which flags such tiles in tile_general).  Other tiles exit at
+// once.  Four CTAs per SM (64 registers; only the rare merge paths spill).
 template <typename T>
 __global__ void __launch_bounds__(HNT, 4) k_tile_hull(const typename KeyOf<T>::K* __restrict__ sorted,
                                                    const TileDesc* __restrict__ htiles,
                                                    const LargeSeg* __restrict__ lsegs,
                                                    const double* __restrict__ lambdas, SegRuntime* rt,
                                                    uint16_t* vp, i128* vx, int32_t* nvert, i128* tile_total,
-                                                   Piece* pieces, int32_t* npieces, int32_t* arrive, int n_hull,
+                                                   const int32_t* __restrict__ tile_general,
                                                    const int32_t* __restrict__ seg_emin, uint32_t* status) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
@@ -495,6 +493,7 @@ __global__ void __launch_bounds__(HNT, 4) k_tile_hull(const typename KeyOf<T>::K
     TileHullSmem& s = *reinterpret_cast<TileHullSmem*>(smem_raw);
     const int t = threadIdx.x;
     const int tile = blockIdx.x;
+    if (!tile_general[tile]) return;
     const TileDesc td = htiles[tile];
     const LargeSeg ls = lsegs[td.lseg];
     const double lam = lambdas[ls.seg];
@@ -579,13 +578,48 @@ __global__ void __launch_bounds__(HNT, 4) k_tile_hull(const typename KeyOf<T>::K
     if (t == 0) {
         nvert[tile] = nv;
         __stcg(reinterpret_cast<uint4*>(tile_total + tile), *reinterpret_cast<const uint4*>(&total));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. the tree of bridge merges across tiles, for segments whose junctions do
+// not resolve locally (seg_mode 2).  One CTA per hull tile; all tile hulls
+// are written.  Each CTA starts its tile's node list, then climbs: at each
+// level the CTA that arrives second merges the two children of the parent;
+// the first one exits.  Nobody waits.
+// ---------------------------------------------------------------------------
+constexpr int CLIMB_CACHE = 1024;   // piece lists up to this long are searched from shared memory
+
+struct ClimbSmem {
+    MergeSmem ms;
+    Piece cache[CLIMB_CACHE];
+    int go;
+    SegConst sc;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(HNT) k_climb(const TileDesc* __restrict__ htiles, const LargeSeg* __restrict__ lsegs,
+                                               const double* __restrict__ lambdas,
+                                               const SegRuntime* __restrict__ rt, const uint16_t* vp, const i128* vx,
+                                               const int32_t* __restrict__ nvert, i128* tile_total, Piece* pieces,
+                                               int32_t* npieces, int32_t* arrive, int n_hull,
+                                               const int32_t* __restrict__ seg_mode) {
+    __shared__ ClimbSmem s;
+    const int t = threadIdx.x;
+    const int tile = blockIdx.x;
+    const TileDesc td = htiles[tile];
+    if (seg_mode[td.lseg] != 2) return;
+    const LargeSeg ls = lsegs[td.lseg];
+    if (t == 0) {
+        double lam = lambdas[ls.seg];
+        if (!(lam >= 0.0) || !(lam <= 1.7976931348623157e308)) lam = 0.0;
+        s.sc = ws_seg_const<T>(ls.len, lam, rt[td.lseg].emax);
         Piece pc;
-        pc.tile = tile; pc.lo = 0; pc.hi = (uint16_t)nv; pc.cum = 0; pc.pad = 0; pc.off = 0;
+        pc.tile = tile; pc.lo = 0; pc.hi = (uint16_t)nvert[tile]; pc.cum = 0; pc.pad = 0; pc.off = 0;
         ws_st_piece(pieces + tile, pc);
         __stcg(npieces + tile, 1);
     }
-    // Climb the merge tree: at each level the CTA that finishes second merges
-    // the two children of the parent; the first one exits.  Nobody waits.
+    __syncthreads();
     const int nt = ls.hull_count, tin = td.tin;
     for (int level = 0; (1 << level) < nt; ++level) {
         const int span = 1 << level;
@@ -601,10 +635,8 @@ __global__ void __launch_bounds__(HNT, 4) k_tile_hull(const typename KeyOf<T>::K
         }
         __syncthreads();
         if (!s.go) break;
-        // the tile's prefix sums are dead during the climb: they cache piece lists
         ws_merge_children(s.ms, pieces, npieces, tile_total, ls.hull_first + parent_base, ls.hull_first + right_base,
-                          vp, vx, ls.hull_first, s.sc, reinterpret_cast<Piece*>(&s.pre),
-                          (int)(sizeof(s.pre) / sizeof(Piece)));
+                          vp, vx, ls.hull_first, s.sc, s.cache, CLIMB_CACHE);
     }
 }
 
@@ -959,15 +991,26 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
     K* sorted = nullptr;
     cudaError_t e = ws_large_sort<T>(W, values, status, spin_limit, st, &sorted);
     if (e) return e;
+    // tile hulls: the lean kernel, then the general one for the tiles it flagged
+    e = ws_large_hull_fast<T>(W, sorted, lambdas, status, st);
+    if (e) return e;
     size_t smem = sizeof(TileHullSmem);
     e = cudaFuncSetAttribute(k_tile_hull<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
+    WS_LAUNCH(W.prof, WSK_TILE_GENERAL, st,
+              (k_tile_hull<T><<<W.n_hull_tiles, HNT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp,
+                                                                W.vx, W.nvert, W.tile_total, W.tile_general,
+                                                                W.seg_emin, status)));
+    // across tiles: junction bridges and the per-segment resolution, then the
+    // tree of merges for the segments that need it
+    e = ws_large_junctions<T>(W, lambdas, st);
+    if (e) return e;
     e = cudaMemsetAsync(W.arrive, 0, sizeof(int32_t) * (size_t)n_levels * W.n_hull_tiles, st);
     if (e) return e;
-    WS_LAUNCH(W.prof, WSK_TILE_HULL, st,
-              (k_tile_hull<T><<<W.n_hull_tiles, HNT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp,
-                                                                W.vx, W.nvert, W.tile_total, W.pieces, W.npieces,
-                                                                W.arrive, W.n_hull_tiles, W.seg_emin, status)));
+    WS_LAUNCH(W.prof, WSK_CLIMB, st,
+              (k_climb<T><<<W.n_hull_tiles, HNT, 0, st>>>(W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp, W.vx, W.nvert,
+                                                          W.tile_total, W.pieces, W.npieces, W.arrive,
+                                                          W.n_hull_tiles, W.seg_mode)));
     e = cudaMemsetAsync(W.tile_piece, 0xff, sizeof(int32_t) * (size_t)W.n_hull_tiles, st);
     if (e) return e;
     WS_LAUNCH(W.prof, WSK_ROOT, st,

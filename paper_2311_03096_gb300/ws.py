@@ -145,6 +145,23 @@ class Context:
     def set_small_max(self, n: int):
         _load().ws_debug_set_small_max(self.handle, int(n))
 
+    def set_ic_cap(self, cap: int):
+        """Round cap of the in-tile Imminent Collisions rounds (0: tree merges only; < 0: default)."""
+        fn = _load().ws_debug_set_ic_cap
+        fn.argtypes = [_vp, ctypes.c_int]
+        fn.restype = None
+        fn(self.handle, int(cap))
+
+    def hull_stats(self, d: int, dtype=torch.float32, n: int = 34):
+        """Tiles of the last prox call for (d, dtype): {"general": g, "capped": c, "rounds": [count of tiles
+        converged after r rounds for r = 0 ..]} (ws_debug_hull_stats)."""
+        fn = _load().ws_debug_hull_stats
+        fn.argtypes = [_vp, _i64, ctypes.c_int, _vp, ctypes.c_int]
+        fn.restype = ctypes.c_int
+        counts = np.zeros(n, np.int64)
+        _check(fn(self.handle, int(d), _dtype_code(dtype), counts.ctypes.data_as(_vp), n), "ws_debug_hull_stats")
+        return {"general": int(counts[0]), "capped": int(counts[1]), "rounds": [int(x) for x in counts[1:]]}
+
     def profile(self, enable: bool):
         """Start (and clear) or stop per-kernel event timing."""
         _check(_load().ws_debug_profile(self.handle, 1 if enable else 0), "ws_debug_profile")
@@ -249,13 +266,30 @@ NOALLOC_MAX_ELEMS = 1 << 20
 def prox_backward_noalloc(grad_out: torch.Tensor, ids: torch.Tensor, grad_in: torch.Tensor, stream=None):
     """Backward for one vector (d <= 2^20) through ws_prox_backward_noalloc: no
     device allocation inside the call; scratch is the library's fixed device
-    array.  For callers that must not allocate where the backward runs."""
+    array.  For callers that must not allocate where the backward runs.
+
+    grad_out and grad_in: contiguous 1-D CUDA tensors of one float dtype and length d
+    (grad_in may be grad_out itself); ids: contiguous int32 CUDA tensor of length d;
+    all three on one device, which is made current for the call."""
+    for name, t in (("grad_out", grad_out), ("ids", ids), ("grad_in", grad_in)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 1-D CUDA tensor")
+    d = grad_out.shape[0]
+    if ids.dtype != torch.int32:
+        raise ValueError("ids must be int32")
+    if grad_in.dtype != grad_out.dtype:
+        raise ValueError("grad_in must have grad_out's dtype")
+    if ids.shape[0] != d or grad_in.shape[0] != d:
+        raise ValueError("grad_out, ids and grad_in must have the same length")
+    if ids.device != grad_out.device or grad_in.device != grad_out.device:
+        raise ValueError("grad_out, ids and grad_in must be on one device")
     lib_ = _load()
     fn = lib_.ws_prox_backward_noalloc
     fn.argtypes = [_vp, _vp, _i64, _vp, ctypes.c_int, _vp]
     fn.restype = ctypes.c_int
-    _check(fn(_ptr(grad_out), _ptr(ids), grad_out.shape[0], _ptr(grad_in), _dtype_code(grad_out.dtype),
-              _stream(stream)), "ws_prox_backward_noalloc")
+    with torch.cuda.device(grad_out.device):
+        _check(fn(_ptr(grad_out), _ptr(ids), d, _ptr(grad_in), _dtype_code(grad_out.dtype), _stream(stream)),
+               "ws_prox_backward_noalloc")
     return grad_in
 
 
