@@ -47,6 +47,8 @@ struct ws_plan {
     int64_t* d_offsets = nullptr;
     int32_t* d_small = nullptr;
     int n_small = 0;
+    int32_t* small_gen = nullptr;     // one-CTA segments passed to the general kernel
+    int32_t* small_gen_count = nullptr;
     double* d_lambda1 = nullptr;   // lambda slot for single-vector calls
     // large path
     int n_lseg = 0, n_sort_tiles = 0, n_hull_tiles = 0;
@@ -217,6 +219,8 @@ ws_status build_plan(ws_plan* p) {
     std::vector<int64_t> offs(p->h_offsets);
     if ((st = plan_upload(p, &p->d_offsets, offs))) return st;
     if ((st = plan_upload(p, &p->d_small, small))) return st;
+    if ((st = plan_alloc(p, (void**)&p->small_gen, sizeof(int32_t) * std::max<size_t>(small.size(), 1)))) return st;
+    if ((st = plan_alloc(p, (void**)&p->small_gen_count, sizeof(int32_t)))) return st;
     if ((st = plan_alloc(p, (void**)&p->d_lambda1, sizeof(double)))) return st;
     if (p->n_lseg == 0) return WS_OK;
     if ((st = plan_upload(p, &p->d_lsegs, lsegs))) return st;
@@ -276,7 +280,8 @@ ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, voi
                       int64_t* n_clusters, ws_prec prec, const WsEpi& ep, cudaStream_t st) {
     const int fp64 = prec == WS_PREC_FP64 ? 1 : 0;
     cudaError_t e = ws_launch_small<T>((const T*)values, p->d_offsets, p->d_small, p->n_small, lambdas, (T*)out, ids,
-                                       n_clusters, fp64, ep, p->ctx->status, st, &p->ctx->prof);
+                                       n_clusters, fp64, ep, p->ctx->status, st, &p->ctx->prof, p->small_gen,
+                                       p->small_gen_count, p->ctx->ic_cap);
     if (e) return map_cuda(e);
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);

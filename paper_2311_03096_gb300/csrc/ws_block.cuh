@@ -22,6 +22,21 @@ template <> __device__ __forceinline__ i128 ws_shfl_up<i128>(i128 v, int delta) 
     return (i128)(((u128)(uint64_t)hi << 64) | (u128)(uint64_t)lo);
 }
 
+// Butterfly shuffle of a sort key (32 or 64 bits).
+__device__ __forceinline__ uint32_t ws_shfl_xor_k(uint32_t v, int o) { return __shfl_xor_sync(WS_FULL_MASK, v, o); }
+__device__ __forceinline__ uint64_t ws_shfl_xor_k(uint64_t v, int o) {
+    return (uint64_t)__shfl_xor_sync(WS_FULL_MASK, (unsigned long long)v, o);
+}
+
+__device__ __forceinline__ void ws_atomic_min_k(uint32_t* p, uint32_t v) { atomicMin(p, v); }
+__device__ __forceinline__ void ws_atomic_max_k(uint32_t* p, uint32_t v) { atomicMax(p, v); }
+__device__ __forceinline__ void ws_atomic_min_k(uint64_t* p, uint64_t v) {
+    atomicMin(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+__device__ __forceinline__ void ws_atomic_max_k(uint64_t* p, uint64_t v) {
+    atomicMax(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
 template <typename V> __device__ __forceinline__ V ws_warp_incl_scan(V v) {
     int lane = threadIdx.x & 31;
 #pragma unroll

@@ -156,6 +156,24 @@ __device__ __forceinline__ SegConst ws_seg_const_L(int64_t d, double lam, int L)
     return c;
 }
 
+// The same constants without FP64 arithmetic (GB300 runs FP64 at a small
+// fraction of the FP32 rate, and a CTA's set-up is on its critical path):
+// the integer fields come from lambda's bits; mu_f = mlam 2^elam / (d - 1)
+// in FP32 (two roundings); mu_d (FP64 values only) on request.
+__device__ __forceinline__ float ws_u64_to_float(uint64_t v);
+__device__ __forceinline__ SegConst ws_seg_const_f(int64_t d, double lam, int L, bool with_mu_d) {
+    SegConst c;
+    c.d = d;
+    c.L = L;
+    int elam;
+    ws_split_lambda(lam, c.mlam, elam);
+    c.s = elam + L;
+    c.dm1 = d > 1 ? (uint64_t)(d - 1) : 1ull;
+    c.mu_f = d > 1 ? ldexpf(ws_u64_to_float(c.mlam), elam) / ws_u64_to_float(c.dm1) : 0.0f;
+    c.mu_d = (with_mu_d && d > 1) ? lam / (double)(d - 1) : 0.0;
+    return c;
+}
+
 template <typename T>
 __device__ __forceinline__ SegConst ws_seg_const(int64_t d, double lam, int emax) {
     SegConst c;

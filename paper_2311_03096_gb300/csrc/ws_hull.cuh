@@ -23,6 +23,47 @@
 #pragma once
 #include "ws_block.cuh"
 
+__device__ __forceinline__ int ws_bitlen_u64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
+
+// range n^2 <= 2^62: every Delta = B n1 - A n2 of a tile of n points whose
+// deviations span `range` is exact in 64 bits (|B n1|, |A n2| <= range n^2 / 4).
+__device__ __forceinline__ bool ws_lean_tile(uint64_t range, int n) {
+    const uint64_t nn = (uint64_t)n * (uint64_t)n;
+    return __umul64hi(range, nn) == 0 && range * nn <= ((uint64_t)1 << 62);
+}
+// range n <= 2^62: every prefix sum of deviations of the tile fits 64 bits
+// (the lean kernels' requirement; Delta may then need the 128-bit test).
+__device__ __forceinline__ bool ws_lean_x(uint64_t range, int n) {
+    return __umul64hi(range, (uint64_t)n) == 0 && range * (uint64_t)n <= ((uint64_t)1 << 62);
+}
+
+// floor(lambda 2^L K / (d - 1)) exactly (the largest D with D (d-1) <= mlam K 2^s),
+// saturated at 2^62.
+static __device__ __noinline__ int64_t ws_floor_muK64(uint64_t K, const SegConst& sc) {
+    if (sc.mlam == 0) return 0;
+    const double est = ldexp((double)sc.mlam * (double)K, sc.s) / (double)sc.dm1;
+    if (!(est < 4.0e18)) return (int64_t)1 << 62;
+    const int64_t q = (int64_t)est;
+    // the estimate is within q 2^-50 + 2 of the answer; bisect a window around it
+    int64_t lo = q > (1 << 14) ? q - (1 << 14) : 0, hi = q + (1 << 14);
+    if (ws_gt_muK(lo, K, sc)) lo = 0;                      // (not reached)
+    if (!ws_gt_muK(hi, K, sc)) return (int64_t)1 << 62;   // (not reached)
+    while (hi - lo > 1) {   // invariant: !gt(lo), gt(hi)
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (ws_gt_muK(mid, K, sc)) hi = mid; else lo = mid;
+    }
+    return lo;
+}
+
+// lambda 2^L / (d - 1) in FP32 for the hull-test filter, without FP64: two
+// roundings (the integer mantissa of lambda, the quotient), covered by the
+// filter's margin.  usable: finite and far from overflow in the filter.
+__device__ __forceinline__ float ws_muq_f(const SegConst& sc, bool& usable) {
+    const float m = ldexpf(ws_u64_to_float(sc.mlam), sc.s) / ws_u64_to_float(sc.dm1);
+    usable = (m == m) && m < 1.0e26f;
+    return usable ? m : 0.0f;
+}
+
 namespace wsh {
 
 constexpr int NT = 256;                // lanes per tile
@@ -48,6 +89,7 @@ struct Smem {
     int wsum[NW];
     int general;                 // a bridge walk hit its cap: the tile needs the general kernel
     int all_conc;
+    int wl[NW], wlr[NW], wf[NW], wfr[NW];   // IC rounds, per warp: last survivor / removal, first ones
 };
 
 __device__ __forceinline__ int own_warp(int p) { return p ? (p - 1) / WP : 0; }
@@ -66,7 +108,7 @@ __device__ __forceinline__ int64_t xat(const Smem& s, int p) {
 // Inline: the sign of Delta, lambda = 0, and the FP32 filter (error bounded
 // relative to Delta + rhs, see TilePtsDev); the rest out of line.
 struct Test {
-    TilePtsDev<M> P;   // (its muq, fast, modd, sodd; P.d64 holds on lean tiles)
+    TilePtsDev<M> P;   // (its muq, fast, modd, sodd, d64)
     SegConst sc;
     __device__ __noinline__ bool slow(int64_t D, uint64_t K) const {
         const int r = P.near_tie64(D, K, sc);
@@ -94,6 +136,7 @@ struct Test {
     }
     __device__ __forceinline__ bool operator()(int a, int64_t Xa, int b, int64_t Xb, int c, int64_t Xc) const {
         const int n1 = b - a, n2 = c - b;
+        if (!P.d64) return P.convex_v(a, Xa, b, Xb, c, Xc, sc);   // Delta may need 128 bits
         const int64_t D = (Xc - Xb) * (int64_t)n1 - (Xb - Xa) * (int64_t)n2;
         if (D <= 0) return false;
         if (P.modd == 0) return true;
@@ -306,7 +349,7 @@ __device__ __forceinline__ int vpt(const Smem& s, const Cur& u) { return (int)s.
 // by walking outward from the junction (the linear merge of two convex
 // chains).  Writes the node result at s.res[g0]; returns false if the walk
 // took more than `cap` steps (result not written).
-__device__ __noinline__ bool node_merge(Smem& s, const Test& T, int g0, int gm, int g1, int cap) {
+static __device__ __noinline__ bool node_merge(Smem& s, const Test& T, int g0, int gm, int g1, int cap) {
     Cur a{last_ne(s, g0, gm), 0};
     a.k = (int)s.hi[a.c] - 1;
     Cur b{first_ne(s, gm, g1), 0};
@@ -486,6 +529,140 @@ __device__ __forceinline__ void cta_tree(Smem& s, const Test& T, int t, int cap)
         if (l == 0) s.ne[w] = m;
     }
     __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Imminent Collisions rounds on the tile as a closed system (appendix
+// algorithm "Imminent collisions algorithm (v2)", Sec. 4), exact.
+//   Round 1 (done by the caller): point p (1 <= p < n) starts a new block iff
+//            y_{p-1} < y_p, i.e. the gap x_p - x_{p-1} exceeds 2 lambda/(d-1).
+//   Round r: every surviving block boundary b, with neighbouring boundaries
+//            a < b < c (0 and n at the ends), stays iff the mean of y over
+//            [a, b) is strictly below the mean over [b, c) -- the hull test
+//            at b; all boundaries are decided at once, as the paper's rounds
+//            do.  A boundary whose neighbours did not change keeps last
+//            round's answer, so only boundaries next to a removal are tested
+//            again.
+// When a round removes nothing, every adjacent pair of blocks has increasing
+// means: the blocks are the tile's pool-adjacent-violators partition and
+// their boundaries (with points 0 and n) the vertices of its lower hull.
+// B: this lane's round-1 boundaries (bit i = point first + i); on return the
+// surviving ones.  Returns true if the rounds converged within `cap` rounds
+// (rounds = rounds run, the final unchanged one included).  Prefix sums of
+// every point must be in s.X (the first barrier here publishes them).  All
+// threads of the CTA call this.
+__device__ __forceinline__ bool ic_rounds(Smem& s, const Test& T, int t, int first, int n, uint32_t& B, int cap,
+                                          int& rounds) {
+    const int l = t & 31, w = t >> 5;
+    rounds = 1;
+    if (!__syncthreads_or(B != 0)) { rounds = 2; return true; }   // one block: the chord (round 2 has nothing to do)
+    uint32_t D = B, Rprev = 0;
+    const int BIG = 1 << 20;
+    while (true) {
+        ++rounds;
+        // neighbouring boundaries outside this lane's range, and where last
+        // round's removals were
+        int lastS = B ? first + 31 - __clz((int)B) : -1, firstS = B ? first + __ffs((int)B) - 1 : BIG;
+        int lastR = Rprev ? first + 31 - __clz((int)Rprev) : -1;
+        int firstR = Rprev ? first + __ffs((int)Rprev) - 1 : BIG;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(WS_FULL_MASK, lastS, o), b = __shfl_up_sync(WS_FULL_MASK, lastR, o);
+            const int c = __shfl_down_sync(WS_FULL_MASK, firstS, o);
+            const int e = __shfl_down_sync(WS_FULL_MASK, firstR, o);
+            if (l >= o) { lastS = max(lastS, a); lastR = max(lastR, b); }
+            if (l + o < 32) { firstS = min(firstS, c); firstR = min(firstR, e); }
+        }
+        // (inclusive scans: lane 31 / lane 0 hold the warp's totals)
+        if (l == 31) { s.wl[w] = lastS; s.wlr[w] = lastR; }
+        if (l == 0) { s.wf[w] = firstS; s.wfr[w] = firstR; }
+        int pS = __shfl_up_sync(WS_FULL_MASK, lastS, 1), pR = __shfl_up_sync(WS_FULL_MASK, lastR, 1);
+        int nS = __shfl_down_sync(WS_FULL_MASK, firstS, 1), nR = __shfl_down_sync(WS_FULL_MASK, firstR, 1);
+        if (l == 0) { pS = -1; pR = -1; }
+        if (l == 31) { nS = BIG; nR = BIG; }
+        __syncthreads();
+        for (int k = 0; k < w; ++k) { pS = max(pS, s.wl[k]); pR = max(pR, s.wlr[k]); }
+        for (int k = w + 1; k < NW; ++k) { nS = min(nS, s.wf[k]); nR = min(nR, s.wfr[k]); }
+        const int prevS = pS < 0 ? 0 : pS, nextS = nS >= BIG ? n : nS;
+        // the end survivors' outer neighbours changed if a removal lay between
+        if (B) {
+            if (pR > prevS) D |= B & (0u - B);
+            if (nR < nextS) D |= 1u << (31 - __clz((int)B));
+        }
+        // decide every boundary to retest against the current blocks
+        uint32_t Rm = 0, bits = B & D;
+        while (bits) {
+            const int i = __ffs((int)bits) - 1;
+            bits &= bits - 1;
+            const int p = first + i;
+            const uint32_t below = B & ((1u << i) - 1u), above = B & ~((2u << i) - 1u);
+            const int a = below ? first + 31 - __clz((int)below) : prevS;
+            const int c = above ? first + __ffs((int)above) - 1 : nextS;
+            if (!T(a, xat(s, a), p, xat(s, p), c, xat(s, c))) Rm |= 1u << i;
+        }
+        if (!__syncthreads_or(Rm != 0)) return true;
+        if (rounds >= cap) return false;
+        // survivors whose in-lane neighbourhood changed
+        const uint32_t B2 = B & ~Rm;
+        D = 0;
+        {
+            uint32_t rest = B2;
+            int pq = -1;
+            while (rest) {
+                const int q = __ffs((int)rest) - 1;
+                rest &= rest - 1;
+                const uint32_t gap = ((1u << q) - 1u) & (pq >= 0 ? ~((2u << pq) - 1u) : 0xffffffffu);
+                if (Rm & gap) { D |= 1u << q; if (pq >= 0) D |= 1u << pq; }
+                pq = q;
+            }
+            if (pq >= 0 && (Rm & ~((2u << pq) - 1u))) D |= 1u << pq;   // removal above the last survivor
+        }
+        Rprev = Rm;
+        B = B2;
+    }
+}
+
+// The tile's hull by per-lane chains (stack form of pool-adjacent-violators),
+// the chord shortcut, a junction-local warp merge or the warp's tree of
+// bridge merges, and the CTA tree.  On return s.lo/s.hi/s.st hold the hull
+// (lane ranges of the lane stacks); returns false if a CTA-level bridge walk
+// took more than cta_cap steps (s.general = 1; the tile needs the general
+// kernel).  Prefix sums of every point must be in s.X.  All threads call
+// this; it ends synchronised.
+__device__ __forceinline__ bool chain_tree_hull(Smem& s, const Test& T, int t, int first, int last, int n, int64_t Xf,
+                                                int cta_cap) {
+    const int l = t & 31, w = t >> 5;
+    __syncthreads();   // (every lane's prefix sums are written)
+    int cnt = 0;
+    if (first < n) cnt = lane_chain(s, T, t, first, last, Xf);
+    s.lo[t] = 0;
+    s.hi[t] = (uint16_t)cnt;
+    __syncthreads();
+    // every chunk hull is its chord and the chain of chunk end points is
+    // concave at every junction: the tile's hull is the chord (0, n)
+    bool conc = true;
+    if (first < n) {
+        conc = cnt == 2;
+        if (conc && last < n) {
+            const int nx = min(last + M, n);
+            conc = !T(first, Xf, last, xat(s, last), nx, xat(s, nx));
+        }
+    }
+    if (__syncthreads_and(conc)) {
+        if (t == 0) { s.st[0] = 0; s.st[NT] = (uint16_t)n; s.hi[0] = 2; }
+        else s.hi[t] = s.lo[t];
+        __syncthreads();
+        return true;
+    }
+    // junction-local merge of the warp's chunks; the warp's tree of merges
+    // only where a bridge reaches past a neighbouring chunk
+    if (!warp_junctions(s, T, t, cnt)) warp_tree(s, T, t);
+    {
+        const unsigned m = __ballot_sync(WS_FULL_MASK, s.hi[t] > s.lo[t]);
+        if (l == 0) s.ne[w] = m;
+    }
+    cta_tree(s, T, t, cta_cap);
+    return !s.general;   // (uniform after cta_tree's barrier)
 }
 
 }  // namespace wsh

@@ -2,7 +2,11 @@
 // float, 2048 for double): one CTA loads a segment once, sorts (key, index)
 // pairs in shared memory, builds the exact hull, and writes values and cluster
 // ids straight to their original positions.  HBM traffic is the I/O floor:
-// read w, write out and id (12 B/element for float).
+// read w, write out and id (12 B/element for float).  The lean kernel
+// (k_small) builds the hull by Imminent Collisions rounds with a fallback to
+// chains and bridge trees; the general kernel (k_small_general) takes the rare
+// segments whose fixed-point sums need 128 bits.
+#include "ws_hull.cuh"
 #include "ws_kernels.cuh"
 
 namespace {
@@ -41,21 +45,22 @@ struct SmallSmem {
     int fast, fastt;
 };
 
+// The general one-CTA prox of one segment (every input, including values
+// whose fixed-point sums need 128 bits): used for the segments the lean
+// kernel below sends here.
 template <typename T, int NT, int M>
-__global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, const int64_t* __restrict__ offsets,
-                                              const int32_t* __restrict__ seg_list, const double* __restrict__ lambdas,
-                                              T* out, int32_t* ids, int64_t* n_clusters, int fp64,
-                                              const WsEpi ep, uint32_t* status) {
+__device__ __forceinline__ void small_general_segment(SmallSmem<T, NT, M>& s, int seg, const T* __restrict__ values,
+                                                      const int64_t* __restrict__ offsets,
+                                                      const double* __restrict__ lambdas, T* out, int32_t* ids,
+                                                      int64_t* n_clusters, int fp64, const WsEpi& ep,
+                                                      uint32_t* status) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     typedef SmallSmem<T, NT, M> S;
     constexpr int CAP = S::CAP;
     constexpr int ITEMS = M;   // items per thread in the sort
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S& s = *reinterpret_cast<S*>(smem_raw);
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
 
-    const int seg = seg_list[blockIdx.x];
     const int64_t a0 = offsets[seg];
     const int n = (int)(offsets[seg + 1] - a0);
     const double lam = lambdas[seg];
@@ -239,6 +244,420 @@ __global__ void __launch_bounds__(NT, 3) k_small(const T* __restrict__ values, c
     if (t == 0 && n_clusters) n_clusters[seg] = c;
 }
 
+template <typename T, int NT, int M>
+__global__ void __launch_bounds__(NT, 3) k_small_general(const T* __restrict__ values,
+                                                      const int64_t* __restrict__ offsets,
+                                                      const int32_t* __restrict__ gen_list,
+                                                      const int32_t* __restrict__ gen_count,
+                                                      const double* __restrict__ lambdas, T* out, int32_t* ids,
+                                                      int64_t* n_clusters, int fp64, const WsEpi ep,
+                                                      uint32_t* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmallSmem<T, NT, M>& s = *reinterpret_cast<SmallSmem<T, NT, M>*>(smem_raw);
+    const int cnt = *gen_count;
+    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+        small_general_segment<T, NT, M>(s, gen_list[i], values, offsets, lambdas, out, ids, n_clusters, fp64, ep,
+                                        status);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The lean one-CTA prox: keys and their original positions sorted in shared
+// memory, then the hull of the sorted segment by the Imminent Collisions
+// rounds with the chain-and-tree fallback (ws_hull.cuh), cluster ids from the
+// cluster-start bitmap, values scattered back through the positions.
+// Segments whose prefix sums need 128 bits (or whose bridge walks are too
+// long) are appended to gen_list for the general kernel above.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct LeanSmem {
+    typedef typename KeyOf<T>::K K;
+    static constexpr int CAP = 16384 / sizeof(K);       // 4096 (float), 2048 (double)
+    // Arrays read in blocks of 16 consecutive entries per thread are padded
+    // (keys: one slot per 16, 16-bit arrays: two) so those reads do not
+    // collide in the shared-memory banks; see kpad / ipad.
+    uint16_t idx[CAP + CAP / 8];                        // original position of every sorted element
+    union {
+        K keys[CAP + CAP / 16];                        // the sort, until the hull starts
+        T vals[CAP];                                    // cluster values, after it
+    } kv;
+    union {
+        struct {
+            uint32_t whist[(wsh::NT / 32) * 256];
+            uint32_t dcount[256], dstart[256];
+        } sort;
+        struct {
+            int cnt[CAP];       // bucket counts, then starts
+        } bucket;
+        wsh::Smem h;
+        uint16_t cid_of[CAP + CAP / 8];   // cluster of every original position (after the values)
+    } u;
+    K kmin, kmax;
+    int bmax;
+    int wsumi[wsh::NT / 32];
+    uint32_t starts[wsh::TILE / 32 + 1];   // bit p: a cluster starts at sorted position p
+    TileScale ts;
+    SegConst sc;    // the segment's global fixed-point scale (cluster values)
+    int flags, emin;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(wsh::NT, 3) k_small(const T* __restrict__ values,
+                                                   const int64_t* __restrict__ offsets,
+                                                   const int32_t* __restrict__ seg_list,
+                                                   const double* __restrict__ lambdas, T* out, int32_t* ids,
+                                                   int64_t* n_clusters, int fp64, const WsEpi ep, uint32_t* status,
+                                                   int32_t* gen_list, int32_t* gen_count, int ic_cap) {
+    typedef KeyOf<T> KO;
+    typedef typename KO::K K;
+    typedef LeanSmem<T> S;
+    constexpr int NT = wsh::NT, M = wsh::M, CAP = S::CAP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S& s = *reinterpret_cast<S*>(smem_raw);
+    wsh::Smem& h = s.u.h;
+    auto kpad = [](int p) { return p + (p >> 4); };          // keys
+    auto ipad = [](int p) { return p + ((p >> 4) << 1); };   // 16-bit arrays
+    const int t = threadIdx.x, l = t & 31, w = t >> 5;
+    const int seg = seg_list[blockIdx.x];
+    const int64_t a0 = offsets[seg];
+    const int n = (int)(offsets[seg + 1] - a0);
+    const double lam = lambdas[seg];
+    if (!(lam >= 0.0) || !(lam <= 1.7976931348623157e308)) {
+        if (t == 0) ws_flag(status, WS_STATUS_BAD_LAMBDA);
+        return;
+    }
+    if (n <= 0 || n > CAP) {
+        if (n > CAP && t == 0) ws_flag(status, WS_STATUS_INTERNAL);
+        if (n == 0 && t == 0 && n_clusters) n_clusters[seg] = 0;
+        return;
+    }
+    // ---- load this thread's 16 consecutive elements (16-byte loads when whole and aligned)
+    const int first = t * M;
+    K key[M];
+    bool bad = false;
+    int emin = 0x7fffffff;
+    {
+        T v[M];
+        const T* src = values + a0 + first;
+        if (first + M <= n && (((uintptr_t)src) & 15) == 0) {
+            constexpr int NV = M * (int)sizeof(T) / 16;
+            uint4 buf[NV];
+#pragma unroll
+            for (int i = 0; i < NV; ++i) buf[i] = __ldcs(reinterpret_cast<const uint4*>(src) + i);
+            const T* bv = reinterpret_cast<const T*>(buf);
+#pragma unroll
+            for (int i = 0; i < M; ++i) v[i] = bv[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) v[i] = (first + i < n) ? src[i] : (T)0;
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (first + i < n) {
+                bad |= !ws_isfinite(v[i]);
+                if (v[i] != (T)0) emin = min(emin, ws_eff_exp(v[i]));
+            }
+            key[i] = KO::to_key(v[i]);
+        }
+    }
+    if (t == 0) s.emin = 0x7fffffff;
+    if (__syncthreads_or(bad)) {
+        if (t == 0) ws_flag(status, WS_STATUS_NONFINITE);
+        return;
+    }
+    if (n == 1) {
+        if (t == 0) {
+            const T x = KO::from_key(key[0]);   // d = 1: no shift (the 1/(d-1) factor is vacuous)
+            out[a0] = fp64 ? (T)ws_epilogue<double>((double)x, 0.0, ep.beta, ep.gamma, ep.on != 0)
+                           : (T)ws_epilogue<float>((float)x, 0.0f, ep.beta_f, ep.gamma_f, ep.on != 0);
+            if (ids) ids[a0] = 0;
+            if (n_clusters) n_clusters[seg] = 1;
+        }
+        return;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emin = min(emin, __shfl_xor_sync(WS_FULL_MASK, emin, o));
+    if (l == 0) atomicMin(&s.emin, emin);
+
+    // ---- sort (key, original position).  First an interpolation bucket sort:
+    // bucket(x) = floor((x - x_min) n / (x_max - x_min)) in FP32 is monotone
+    // in x (every step rounds monotonically), so equal keys share a bucket and
+    // sorting each bucket by key sorts the segment; for the smooth
+    // distributions of weights a bucket holds a few elements.  If a bucket is
+    // larger than BUCKET_MAX the segment takes the LSD radix passes instead.
+    constexpr int BUCKET_MAX = 32;
+    if (t == 0) { s.kmin = ~(K)0; s.kmax = 0; s.bmax = 0; }
+    {
+        K lo = ~(K)0, hi = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (first + i < n) { lo = min(lo, key[i]); hi = max(hi, key[i]); }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, ws_shfl_xor_k(lo, o));
+            hi = max(hi, ws_shfl_xor_k(hi, o));
+        }
+        int* cnt = s.u.bucket.cnt;
+        for (int i = t; i < n; i += NT) cnt[i] = 0;
+        __syncthreads();
+        if (l == 0) { ws_atomic_min_k(&s.kmin, lo); ws_atomic_max_k(&s.kmax, hi); }
+    }
+    __syncthreads();
+    bool radix = false;
+    {
+        int* cnt = s.u.bucket.cnt;
+        const float f0 = (float)KO::from_key(s.kmin), f1 = (float)KO::from_key(s.kmax);
+        const float span = f1 - f0;
+        const float scale = (span > 0.0f && span <= 3.0e38f) ? (float)n / span : 0.0f;
+        int bk[M], rk[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (first + i < n) {
+                const float f = ((float)KO::from_key(key[i]) - f0) * scale;
+                bk[i] = min(n - 1, max(0, (int)f));
+                rk[i] = atomicAdd(&cnt[bk[i]], 1);
+            }
+        }
+        __syncthreads();
+        // bucket starts: this thread's 16 consecutive buckets, then the CTA scan
+        int c[M], sum = 0, big = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            c[i] = (first + i < n) ? cnt[first + i] : 0;
+            sum += c[i];
+            big = max(big, c[i]);
+        }
+        int tot;
+        int run = ws_block_excl_scan<NT, int>(sum, s.wsumi, &tot);
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            if (first + i < n) { cnt[first + i] = run; run += c[i]; }
+        radix = __syncthreads_or(big > BUCKET_MAX);
+        if (!radix) {
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+                if (first + i < n) {
+                    const int pp = cnt[bk[i]] + rk[i];
+                    s.kv.keys[kpad(pp)] = key[i];
+                    s.idx[ipad(pp)] = (uint16_t)(first + i);
+                }
+            __syncthreads();
+            // each bucket by key (insertion sort; ties may end in any order)
+#pragma unroll 1
+            for (int i = 0; i < M; ++i) {
+                if (first + i >= n || c[i] < 2) continue;
+                const int b0 = cnt[first + i], b1 = b0 + c[i];
+                for (int a = b0 + 1; a < b1; ++a) {
+                    const K kk = s.kv.keys[kpad(a)];
+                    const uint16_t ii = s.idx[ipad(a)];
+                    int j = a - 1;
+                    while (j >= b0 && s.kv.keys[kpad(j)] > kk) {
+                        s.kv.keys[kpad(j + 1)] = s.kv.keys[kpad(j)];
+                        s.idx[ipad(j + 1)] = s.idx[ipad(j)];
+                        --j;
+                    }
+                    s.kv.keys[kpad(j + 1)] = kk;
+                    s.idx[ipad(j + 1)] = ii;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- otherwise: LSD radix sort, 8-bit digits.  The first pass ranks the
+    // loaded elements directly (any order is fine before the first pass);
+    // later passes take position w*32*M + k*32 + l of the previous one, which
+    // the stable ranking keeps in order.
+    for (int pass = 0; radix && pass < KO::BITS / 8; ++pass) {
+        uint16_t ii[M];
+        uint32_t dg[M];
+        bool valid[M];
+        int pos[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            if (pass == 0) {
+                valid[k] = first + k < n;
+                ii[k] = (uint16_t)(first + k);
+            } else {
+                const int p = w * 32 * M + k * 32 + l;
+                valid[k] = p < n;
+                key[k] = valid[k] ? s.kv.keys[kpad(p)] : (K)0;
+                ii[k] = valid[k] ? s.idx[ipad(p)] : (uint16_t)0;
+            }
+            dg[k] = (uint32_t)((key[k] >> (8 * pass)) & 0xff);
+        }
+        __syncthreads();
+        ws_rank_digits<NT, M, 1>(dg, valid, pos, s.u.sort.whist, s.u.sort.dcount, s.u.sort.dstart);
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (valid[k]) { s.kv.keys[kpad(pos[k])] = key[k]; s.idx[ipad(pos[k])] = ii[k]; }
+        __syncthreads();
+    }
+
+    // ---- the sorted segment as one hull tile: this thread's 16 sorted keys
+    K kr[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) kr[i] = (first + i < n) ? s.kv.keys[kpad(first + i)] : s.kv.keys[0];
+    const K kfirst = s.kv.keys[0], klast = s.kv.keys[kpad(n - 1)];
+    const K kprev = (t > 0 && first < n) ? s.kv.keys[kpad(first - 1)] : kfirst;
+    const T xlo = KO::from_key(kfirst), xhi = KO::from_key(klast);
+    const int emax = ws_fix_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), s.emin);
+    int sh;
+    const bool bin = ws_tile_binade<T>(kfirst, klast, n, emax, sh);
+    const int64_t q0 = ws_fixed<T>(xlo, emax);
+    const uint64_t range = bin ? (uint64_t)(klast - kfirst) : (uint64_t)(ws_fixed<T>(xhi, emax) - q0);
+    const bool lean = ws_lean_x(range, n);   // prefix sums in 64 bits
+    const bool d64 = ws_lean_tile(range, n);  // every Delta too
+    if (!lean) {   // (uniform)
+        if (t == 0) gen_list[atomicAdd(gen_count, 1)] = seg;
+        return;
+    }
+    if (t == 0) {   // (no FP64 on this critical path)
+        s.sc = ws_seg_const_f(n, lam, KO::L_BASE - emax, fp64 != 0);
+        TileScale& ts = s.ts;
+        ts.sc = bin ? ws_seg_const_f(n, lam, s.sc.L - sh, false) : s.sc;
+        bool f;
+        ts.muq = ws_muq_f(ts.sc, f);
+        ts.fast = f ? 1 : 0;
+        if (ts.sc.mlam == 0) { ts.modd = 0; ts.sodd = 0; }
+        else { const int tz = __ffsll((long long)ts.sc.mlam) - 1; ts.modd = ts.sc.mlam >> tz; ts.sodd = ts.sc.s + tz; }
+        h.general = 0;
+    }
+    auto devk = [&](K k) -> int64_t {
+        return bin ? (int64_t)(k - kfirst) : ws_fixed<T>(KO::from_key(k), emax) - q0;
+    };
+    auto dev = [&](int i) -> int64_t { return devk(kr[i]); };
+    int64_t csum = 0;
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+        if (first + i < n) csum += dev(i);
+    const int64_t winc = ws_warp_incl_scan<long long>((long long)csum);
+    __syncthreads();   // (the sort's scratch is dead: the hull's shared memory may be written)
+    if (l == 31) h.wtot[w] = winc;
+    if (t == 0) wsh::xref(h, 0) = 0;
+    __syncthreads();
+    int64_t wbase = 0;
+    for (int k = 0; k < w; ++k) wbase += h.wtot[k];
+    const int64_t Xf = wbase + winc - csum;
+    const int last = min(first + M, n);
+    if (first < n) wsh::lane_prefix(h, first, last, Xf, dev);
+    wsh::Test tst;
+    tst.sc = s.ts.sc;
+    tst.P.s64 = nullptr;
+    tst.P.muq = s.ts.muq;
+    tst.P.fast = s.ts.fast != 0;
+    tst.P.d64 = d64;
+    tst.P.thr = nullptr;
+    tst.P.modd = s.ts.modd;
+    tst.P.sodd = s.ts.sodd;
+    // round 1 of the Imminent Collisions rounds: boundaries where neighbours do
+    // not collide (the hull test on the consecutive points p-1, p, p+1)
+    uint32_t B = 0;
+    {
+        int64_t dprev = devk(kprev);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int p = first + i;
+            const int64_t di = dev(i);
+            if (p >= 1 && p < n && tst(p - 1, 0, p, dprev, p + 1, dprev + di)) B |= 1u << i;
+            dprev = di;
+        }
+    }
+    int rounds = 0;
+    bool converged = false;
+    if (ic_cap > 0) converged = wsh::ic_rounds(h, tst, t, first, n, B, ic_cap, rounds);
+    uint16_t* st16 = reinterpret_cast<uint16_t*>(s.starts);
+    if (converged) {
+        st16[t] = (uint16_t)(B | (t == 0 ? 1u : 0u));
+    } else {
+        if (!wsh::chain_tree_hull(h, tst, t, first, last, n, Xf, 1 << 30)) {   // (no cap: never fails)
+            if (t == 0) gen_list[atomicAdd(gen_count, 1)] = seg;
+            return;
+        }
+        st16[t] = 0;
+        __syncthreads();
+        for (int k = h.lo[t]; k < (int)h.hi[t]; ++k) {
+            const int p = h.st[k * NT + t];
+            if (p < n) atomicOr(&s.starts[p >> 5], 1u << (p & 31));
+        }
+    }
+    __syncthreads();
+    // ---- cluster ids: rank of every start; values of the clusters this thread starts
+    const uint32_t mine = (uint32_t)st16[t] & (first < n ? (n - first >= M ? 0xffffu : ((1u << (n - first)) - 1u)) : 0u);
+    int C;
+    const int base = ws_block_excl_scan<NT, int>(__popc(mine), h.wsum, &C);
+    const float x0f = (float)xlo;
+    {
+        uint32_t rest = mine;
+        int r = base;
+        while (rest) {
+            const int i = __ffs((int)rest) - 1;
+            rest &= rest - 1;
+            const int a = first + i;
+            // end of the cluster: the next start (in this thread, else the next set bit of the bitmap), or n
+            int b = n;
+            if (rest) b = first + __ffs((int)rest) - 1;
+            else {
+                for (int wd = (first + M) >> 5; (wd << 5) < n; ++wd) {
+                    uint32_t bits = s.starts[wd];
+                    if ((wd << 5) < first + M) bits &= 0xffffffffu << ((first + M) & 31);
+                    if (bits) { b = min((wd << 5) + __ffs((int)bits) - 1, n); break; }
+                }
+            }
+            const int64_t xd = wsh::xat(h, b) - wsh::xat(h, a);
+            if (KO::BITS == 32 && !fp64) {
+                // FP32: mean = x_0 + (deviation sum / count) in tile units; every
+                // term exact but the conversions (a few FP32 ulps of max |w|)
+                const float xa = (float)KO::from_key(kr[i]);
+                const float mean = (b - a == 1) ? xa
+                                                : x0f + ldexpf(ws_u64_to_float((uint64_t)xd) / (float)(b - a), -s.ts.sc.L);
+                s.kv.vals[r] = (T)ws_epilogue<float>(mean, s.sc.mu_f * (float)(n - a - b), ep.beta_f, ep.gamma_f,
+                                                     ep.on != 0);
+            } else {
+                const i128 SX = (i128)(b - a) * (i128)q0 + (bin ? ((i128)xd << sh) : (i128)xd);
+                s.kv.vals[r] = ValueOut<T>::value(SX, a, b, KO::from_key(kr[i]), s.sc, fp64 != 0, ep);
+            }
+            ++r;
+        }
+    }
+    __syncthreads();   // (the prefix sums are dead: their storage takes the cluster of every position)
+    // ---- the cluster of every original position, then this thread's 16
+    // consecutive outputs (coalesced stores)
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const int p = first + i;
+        if (p < n) s.u.cid_of[ipad(s.idx[ipad(p)])] = (uint16_t)(base + __popc(mine & ((2u << i) - 1u)) - 1);
+    }
+    __syncthreads();
+    if (first < n) {
+        T ov[M];
+        int32_t oi[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int c = (first + i < n) ? (int)s.u.cid_of[ipad(first + i)] : 0;
+            oi[i] = c;
+            ov[i] = s.kv.vals[c];
+        }
+        T* od = out + a0 + first;
+        int32_t* id = ids ? ids + a0 + first : nullptr;
+        if (first + M <= n && (((uintptr_t)od) & 15) == 0 && (!id || (((uintptr_t)id) & 15) == 0)) {
+            constexpr int VT = 16 / (int)sizeof(T);
+#pragma unroll
+            for (int i = 0; i < M; i += VT) __stcs(reinterpret_cast<uint4*>(od + i), *reinterpret_cast<const uint4*>(ov + i));
+            if (id) {
+#pragma unroll
+                for (int i = 0; i < M; i += 4) __stcs(reinterpret_cast<uint4*>(id + i), *reinterpret_cast<const uint4*>(oi + i));
+            }
+        } else {
+            for (int i = 0; i < M && first + i < n; ++i) {
+                od[i] = ov[i];
+                if (id) id[i] = oi[i];
+            }
+        }
+    }
+    if (t == 0 && n_clusters) n_clusters[seg] = C;
+}
+
 // Backward for short segments: per-cluster mean of grad_out (shared-memory sums).
 template <typename T, int NT, int CAP>
 __global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, const int32_t* __restrict__ ids,
@@ -275,17 +694,28 @@ __global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, 
 template <typename T>
 cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
                             const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
-                            const WsEpi& ep, uint32_t* status, cudaStream_t st, WsProf* prof) {
+                            const WsEpi& ep, uint32_t* status, cudaStream_t st, WsProf* prof, int32_t* gen_list,
+                            int32_t* gen_count, int ic_cap) {
     constexpr int NT = 256;
     constexpr int M = SmallCfg<T>::M;
     if (n_list <= 0) return cudaSuccess;
-    size_t smem = sizeof(SmallSmem<T, NT, M>);
-    auto kern = k_small<T, NT, M>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaMemsetAsync(gen_count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(LeanSmem<T>);
+    e = cudaFuncSetAttribute(k_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     WS_LAUNCH(prof, WSK_SMALL, st,
-              (kern<<<n_list, NT, smem, st>>>(values, offsets, seg_list, lambdas, out, ids, n_clusters, fp64, ep,
-                                              status)));
+              (k_small<T><<<n_list, NT, smem, st>>>(values, offsets, seg_list, lambdas, out, ids, n_clusters, fp64, ep,
+                                                    status, gen_list, gen_count, ic_cap)));
+    // the segments the lean kernel passed on (none on ordinary inputs): a
+    // small grid that walks the list
+    const size_t gsmem = sizeof(SmallSmem<T, NT, M>);
+    auto gk = k_small_general<T, NT, M>;
+    e = cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsmem);
+    if (e != cudaSuccess) return e;
+    WS_LAUNCH(prof, WSK_SMALL, st,
+              (gk<<<n_list < 456 ? n_list : 456, NT, gsmem, st>>>(values, offsets, gen_list, gen_count, lambdas, out, ids,
+                                                               n_clusters, fp64, ep, status)));
     return cudaGetLastError();
 }
 
@@ -300,10 +730,11 @@ cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64
 }
 
 template cudaError_t ws_launch_small<float>(const float*, const int64_t*, const int32_t*, int, const double*, float*,
-                                            int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t, WsProf*);
+                                            int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t, WsProf*,
+                                            int32_t*, int32_t*, int);
 template cudaError_t ws_launch_small<double>(const double*, const int64_t*, const int32_t*, int, const double*,
                                              double*, int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t,
-                                             WsProf*);
+                                             WsProf*, int32_t*, int32_t*, int);
 template cudaError_t ws_launch_small_backward<float>(const float*, const int32_t*, const int64_t*, const int32_t*,
                                                      int, float*, uint32_t*, cudaStream_t, WsProf*);
 template cudaError_t ws_launch_small_backward<double>(const double*, const int32_t*, const int64_t*,

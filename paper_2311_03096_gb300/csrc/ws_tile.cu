@@ -39,24 +39,6 @@ constexpr int CTA_WALK_CAP = 512;
 // ---------------------------------------------------------------------------
 // Per-segment scale constants (one CTA of WS_NSCALE threads per segment)
 // ---------------------------------------------------------------------------
-// floor(lambda 2^L K / (d - 1)) exactly (the largest D with D (d-1) <= mlam K 2^s),
-// saturated at 2^62.
-__device__ int64_t ws_floor_muK64(uint64_t K, const SegConst& sc) {
-    if (sc.mlam == 0) return 0;
-    const double est = ldexp((double)sc.mlam * (double)K, sc.s) / (double)sc.dm1;
-    if (!(est < 4.0e18)) return (int64_t)1 << 62;
-    const int64_t q = (int64_t)est;
-    // the estimate is within q 2^-50 + 2 of the answer; bisect a window around it
-    int64_t lo = q > (1 << 14) ? q - (1 << 14) : 0, hi = q + (1 << 14);
-    if (ws_gt_muK(lo, K, sc)) lo = 0;                      // (not reached)
-    if (!ws_gt_muK(hi, K, sc)) return (int64_t)1 << 62;   // (not reached)
-    while (hi - lo > 1) {   // invariant: !gt(lo), gt(hi)
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (ws_gt_muK(mid, K, sc)) hi = mid; else lo = mid;
-    }
-    return lo;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(WS_NSCALE) k_scales(const typename KeyOf<T>::K* __restrict__ sorted,
                                                       const LargeSeg* __restrict__ lsegs,
@@ -94,10 +76,7 @@ __global__ void __launch_bounds__(WS_NSCALE) k_scales(const typename KeyOf<T>::K
 struct FastSmem {
     wsh::Smem h;
     TileScale ts;
-    int wl[NW], wlr[NW], wf[NW], wfr[NW];   // per warp: last survivor / removal, first survivor / removal
 };
-
-__device__ __forceinline__ int ws_bitlen_u64(uint64_t v) { return v ? 64 - __clzll((long long)v) : 0; }
 
 // Tile hull: Imminent Collisions rounds (appendix algorithm "Imminent
 // collisions algorithm (v2)", Sec. 4) on the tile as a closed system, with
@@ -139,8 +118,8 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
     const bool bin = ws_tile_binade<T>(kfirst, klast, n, emax, sh);
     const int64_t q0 = ws_fixed<T>(KO::from_key(kfirst), emax);
     const uint64_t range = bin ? (uint64_t)(klast - kfirst) : (uint64_t)(ws_fixed<T>(KO::from_key(klast), emax) - q0);
-    // every Delta = B n1 - A n2 exact in 64 bits: range n^2 <= 2^62 (implies range n <= 2^62)
-    const bool lean = ws_bitlen_u64(range) + 2 * ws_bitlen_u64((uint64_t)n) <= 62;
+    const bool lean = ws_lean_x(range, n);   // prefix sums in 64 bits
+    const bool d64 = ws_lean_tile(range, n);  // every Delta too
     if (t == 0) {
         tile_general[tile] = lean ? 0 : 1;
         if (!lean) tile_rounds[tile] = -2;
@@ -191,7 +170,7 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
     tst.P.s64 = nullptr;
     tst.P.muq = S.ts.muq;
     tst.P.fast = S.ts.fast != 0;
-    tst.P.d64 = true;
+    tst.P.d64 = d64;
     tst.P.thr = nullptr;
     tst.P.modd = S.ts.modd;
     tst.P.sodd = S.ts.sodd;
@@ -210,121 +189,18 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
             dprev = di;
         }
     }
-    int rounds = 1;
+    int rounds = 0;
     bool converged = false;
-    if (ic_cap > 0) {
-        // (this barrier also publishes every lane's prefix sums)
-        if (!__syncthreads_or(B != 0)) {
-            converged = true;   // one block: the tile's hull is its chord (round 2 has nothing to test)
-            rounds = 2;
-        } else {
-            uint32_t D = B, Rprev = 0;
-            const int BIG = 1 << 20;
-            while (true) {
-                ++rounds;
-                // neighbouring boundaries outside this lane's range, and where
-                // last round's removals were
-                int lastS = B ? first + 31 - __clz((int)B) : -1, firstS = B ? first + __ffs((int)B) - 1 : BIG;
-                int lastR = Rprev ? first + 31 - __clz((int)Rprev) : -1;
-                int firstR = Rprev ? first + __ffs((int)Rprev) - 1 : BIG;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int a = __shfl_up_sync(WS_FULL_MASK, lastS, o), b = __shfl_up_sync(WS_FULL_MASK, lastR, o);
-                    const int c = __shfl_down_sync(WS_FULL_MASK, firstS, o);
-                    const int e = __shfl_down_sync(WS_FULL_MASK, firstR, o);
-                    if (l >= o) { lastS = max(lastS, a); lastR = max(lastR, b); }
-                    if (l + o < 32) { firstS = min(firstS, c); firstR = min(firstR, e); }
-                }
-                // (inclusive scans: lane 31 / lane 0 hold the warp's totals)
-                if (l == 31) { S.wl[w] = lastS; S.wlr[w] = lastR; }
-                if (l == 0) { S.wf[w] = firstS; S.wfr[w] = firstR; }
-                int pS = __shfl_up_sync(WS_FULL_MASK, lastS, 1), pR = __shfl_up_sync(WS_FULL_MASK, lastR, 1);
-                int nS = __shfl_down_sync(WS_FULL_MASK, firstS, 1), nR = __shfl_down_sync(WS_FULL_MASK, firstR, 1);
-                if (l == 0) { pS = -1; pR = -1; }
-                if (l == 31) { nS = BIG; nR = BIG; }
-                __syncthreads();
-                for (int k = 0; k < w; ++k) { pS = max(pS, S.wl[k]); pR = max(pR, S.wlr[k]); }
-                for (int k = w + 1; k < NW; ++k) { nS = min(nS, S.wf[k]); nR = min(nR, S.wfr[k]); }
-                const int prevS = pS < 0 ? 0 : pS, nextS = nS >= BIG ? n : nS;
-                // the end survivors' outer neighbours changed if a removal lay between
-                if (B) {
-                    if (pR > prevS) D |= B & (0u - B);
-                    if (nR < nextS) D |= 1u << (31 - __clz((int)B));
-                }
-                // decide every boundary to retest against the current blocks
-                uint32_t Rm = 0, bits = B & D;
-                while (bits) {
-                    const int i = __ffs((int)bits) - 1;
-                    bits &= bits - 1;
-                    const int p = first + i;
-                    const uint32_t below = B & ((1u << i) - 1u), above = B & ~((2u << i) - 1u);
-                    const int a = below ? first + 31 - __clz((int)below) : prevS;
-                    const int c = above ? first + __ffs((int)above) - 1 : nextS;
-                    if (!tst(a, wsh::xat(s, a), p, wsh::xat(s, p), c, wsh::xat(s, c))) Rm |= 1u << i;
-                }
-                const int any = __syncthreads_or(Rm != 0);
-                if (!any) { converged = true; break; }
-                if (rounds >= ic_cap) break;
-                // survivors whose in-lane neighbourhood changed
-                const uint32_t B2 = B & ~Rm;
-                D = 0;
-                {
-                    uint32_t rest = B2;
-                    int pq = -1;
-                    while (rest) {
-                        const int q = __ffs((int)rest) - 1;
-                        rest &= rest - 1;
-                        const uint32_t gap = ((1u << q) - 1u) & (pq >= 0 ? ~((2u << pq) - 1u) : 0xffffffffu);
-                        if (Rm & gap) { D |= 1u << q; if (pq >= 0) D |= 1u << pq; }
-                        pq = q;
-                    }
-                    if (pq >= 0 && (Rm & ~((2u << pq) - 1u))) D |= 1u << pq;   // removal above the last survivor
-                }
-                Rprev = Rm;
-                B = B2;
-            }
-        }
-    }
+    if (ic_cap > 0) converged = wsh::ic_rounds(s, tst, t, first, n, B, ic_cap, rounds);
     if (t == 0) tile_rounds[tile] = converged ? rounds : -1;
-
     int c;      // vertices this lane writes
     int lo = 0;
     if (converged) {
         c = __popc(B) + (t == 0 ? 1 : 0) + (first < n && last == n ? 1 : 0);
     } else {
-        __syncthreads();   // (every lane's prefix sums are written)
-        int cnt = 0;
-        if (first < n) cnt = wsh::lane_chain(s, tst, t, first, last, Xf);
-        s.lo[t] = 0;
-        s.hi[t] = (uint16_t)cnt;
-        __syncthreads();
-        // shortcut: every chunk hull is its chord and the chain of chunk end
-        // points is concave at every junction: the tile's hull is the chord (0, n)
-        bool conc = true;
-        if (first < n) {
-            conc = cnt == 2;
-            if (conc && last < n) {
-                const int nx = min(last + M, n);
-                conc = !tst(first, Xf, last, wsh::xat(s, last), nx, wsh::xat(s, nx));
-            }
-        }
-        if (__syncthreads_and(conc)) {
-            if (t == 0) { s.st[0] = 0; s.st[NT] = (uint16_t)n; s.hi[0] = 2; }
-            else s.hi[t] = s.lo[t];
-            __syncthreads();
-        } else {
-            // junction-local merge of the warp's chunks; the warp's tree of
-            // merges only where a bridge reaches past a neighbouring chunk
-            if (!wsh::warp_junctions(s, tst, t, cnt)) wsh::warp_tree(s, tst, t);
-            {
-                const unsigned m = __ballot_sync(WS_FULL_MASK, s.hi[t] > s.lo[t]);
-                if (l == 0) s.ne[w] = m;
-            }
-            wsh::cta_tree(s, tst, t, CTA_WALK_CAP);
-            if (s.general) {   // (uniform after cta_tree's barrier)
-                if (t == 0) { tile_general[tile] = 1; tile_rounds[tile] = -2; }
-                return;
-            }
+        if (!wsh::chain_tree_hull(s, tst, t, first, last, n, Xf, CTA_WALK_CAP)) {
+            if (t == 0) { tile_general[tile] = 1; tile_rounds[tile] = -2; }
+            return;
         }
         lo = s.lo[t];
         c = (int)s.hi[t] - lo;
