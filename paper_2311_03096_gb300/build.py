@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libws_prox.so")
-SOURCES = ["ws_small.cu", "ws_sort.cu", "ws_large.cu", "ws_tile.cu", "ws_stats.cu", "ws_api.cu", "ws_noalloc.cu"]
+SOURCES = ["ws_small.cu", "ws_sort.cu", "ws_large.cu", "ws_tile.cu", "ws_bwd.cu", "ws_stats.cu", "ws_api.cu", "ws_noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -89,6 +89,8 @@ struct ws_plan {
     void* stat_partial = nullptr;
     void* bsum = nullptr;
     int32_t* bcnt = nullptr;
+    unsigned long long* bacc = nullptr;
+    int32_t* bwd_seg = nullptr;
 };
 
 namespace {
@@ -135,6 +137,8 @@ LargeWork<T> make_work(const ws_plan* p) {
     W.dir = p->dir;
     W.bsum = (T*)p->bsum;
     W.bcnt = p->bcnt;
+    W.bacc = p->bacc;
+    W.bwd_seg = p->bwd_seg;
     W.prof = &p->ctx->prof;
     return W;
 }
@@ -263,6 +267,8 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->dir, sizeof(DirEntry) * (size_t)dir_pos))) return st;
     if ((st = plan_alloc(p, &p->bsum, vsize * slots))) return st;
     if ((st = plan_alloc(p, (void**)&p->bcnt, sizeof(int32_t) * slots))) return st;
+    if ((st = plan_alloc(p, (void**)&p->bacc, 2 * sizeof(unsigned long long) * slots))) return st;
+    if ((st = plan_alloc(p, (void**)&p->bwd_seg, 2 * sizeof(int32_t) * p->n_lseg))) return st;
     if (cudaMemset(p->rt, 0, sizeof(SegRuntime) * p->n_lseg) != cudaSuccess) return WS_ERR_CUDA;
     return WS_OK;
 }

@@ -47,6 +47,17 @@ template <typename V> __device__ __forceinline__ V ws_warp_incl_scan(V v) {
     return v;
 }
 
+// Warp sum of a 128-bit integer (every lane gets it).
+__device__ __forceinline__ i128 ws_warp_reduce_i128(i128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long lo = __shfl_xor_sync(WS_FULL_MASK, (long long)(uint64_t)v, o);
+        const long long hi = __shfl_xor_sync(WS_FULL_MASK, (long long)(uint64_t)((u128)v >> 64), o);
+        v += (i128)(((u128)(uint64_t)hi << 64) | (u128)(uint64_t)lo);
+    }
+    return v;
+}
+
 // Block exclusive scan; returns the exclusive prefix, *total gets the sum.
 // `wsum` is NT/32 elements of shared scratch.  Contains __syncthreads.
 template <int NT, typename V>

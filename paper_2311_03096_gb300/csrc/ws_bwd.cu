@@ -1,0 +1,298 @@
+// ws_bwd.cu -- the backward of the prox with the partition held fixed: every
+// element's gradient is the mean of grad_out over its cluster (the Jacobian
+// of the cluster means; a cluster moves as one particle, Sec. 3).
+//
+// The cluster sums are exact and deterministic: every grad_out value is
+// converted to a 128-bit integer at a per-segment scale (exact for values
+// within SH binades of the segment's largest |g|: 71 for float, 42 for
+// double; smaller ones keep their top bits), and the integers are added with
+// 64-bit atomics that carry into the high word explicitly.  Integer addition
+// is associative, so the sum -- hence the mean -- does not depend on the
+// order of the additions, and its error does not grow with the cluster size
+// (one rounding when the mean is formed).
+//
+// Large segments: per-segment scale and largest id (k_bwd_prep), the used
+// cluster slots cleared (k_bwd_zero), the sums (k_bwd_accum: lanes of a warp
+// with the same cluster add once, and a tile whose elements all share one
+// cluster adds once per CTA, so a single huge cluster costs one atomic per
+// 8192 elements), the means (k_bwd_mean), the gather (k_bwd_apply).
+// One-CTA segments: the same arithmetic in shared memory (k_small_backward).
+#include "ws_kernels.cuh"
+
+namespace {
+
+constexpr int BNT = 256;
+constexpr int BTILE = WS_SORT_TILE;   // elements per CTA (the sort tiles of the plan)
+
+template <typename T> struct BwdFix;
+template <> struct BwdFix<float> { static constexpr int SH = 71, BIAS = 127, MANT = 23; };
+template <> struct BwdFix<double> { static constexpr int SH = 42, BIAS = 1023, MANT = 52; };
+
+// g * 2^(SH - emax + BIAS + MANT) as an integer (exact unless g is more than
+// SH binades below 2^emax; then truncated toward zero).
+template <typename T>
+__device__ __forceinline__ i128 ws_bwd_fix(T g, int emax) {
+    typedef KeyOf<T> KO;
+    const uint64_t b = (uint64_t)KO::bits(g);
+    int e = (int)((b >> KO::MANT) & KO::EXPMASK);
+    uint64_t m = b & ((1ull << KO::MANT) - 1ull);
+    if (e == 0) e = 1; else m |= (1ull << KO::MANT);
+    const int sh = e - emax + BwdFix<T>::SH;
+    u128 mag;
+    if (sh >= 0) mag = (u128)m << sh;
+    else mag = (sh > -64) ? (u128)(m >> (-sh)) : (u128)0;
+    const bool neg = (b >> (KO::BITS - 1)) & 1ull;
+    return neg ? -(i128)mag : (i128)mag;
+}
+
+// mean = S / cnt * 2^-(SH - emax + BIAS + MANT)
+template <typename T>
+__device__ __forceinline__ T ws_bwd_mean(i128 S, int cnt, int emax) {
+    const int Lg = BwdFix<T>::SH - emax + BwdFix<T>::BIAS + BwdFix<T>::MANT;
+    if (sizeof(T) == 4) return (T)ldexpf(ws_i128_to_float_scaled(S, 0) / (float)cnt, -Lg);
+    return (T)ldexp(ws_i128_to_double(S) / (double)cnt, -Lg);
+}
+
+__device__ __forceinline__ void ws_atomic_add_i128(unsigned long long* lo_hi, i128 v) {
+    const unsigned long long lo = (unsigned long long)(uint64_t)v;
+    const unsigned long long hi = (unsigned long long)(uint64_t)((u128)v >> 64);
+    const unsigned long long old = atomicAdd(lo_hi, lo);
+    atomicAdd(lo_hi + 1, hi + (old + lo < old ? 1ull : 0ull));
+}
+
+template <typename T> __device__ __forceinline__ int ws_g_exp(T g) { return g != (T)0 ? ws_eff_exp(g) : 0; }
+
+// 1. per segment: largest exponent of grad_out and largest cluster id
+template <typename T>
+__global__ void __launch_bounds__(BNT) k_bwd_prep(const T* __restrict__ g, const int32_t* __restrict__ ids,
+                                                  const TileDesc* __restrict__ tiles,
+                                                  const LargeSeg* __restrict__ lsegs, int32_t* seg_emax,
+                                                  int32_t* seg_maxid, uint32_t* status) {
+    const TileDesc td = tiles[blockIdx.x];
+    const LargeSeg ls = lsegs[td.lseg];
+    int e = 0, mx = -1;
+    bool bad = false;
+    for (int i = threadIdx.x; i < td.len; i += BNT) {
+        e = max(e, ws_g_exp(g[td.vpos + i]));
+        const int id = ids[td.vpos + i];
+        if (id < 0 || (int64_t)id >= ls.len) bad = true;
+        else mx = max(mx, id);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(seg_emax + td.lseg, e);
+        atomicMax(seg_maxid + td.lseg, mx);
+    }
+    if (bad) ws_flag(status, WS_STATUS_INTERNAL);
+}
+
+// 2. clear the slots of ids 0 .. max id (tile k of a segment clears slots
+// [k BTILE, (k + 1) BTILE): a segment has at most len slots)
+__global__ void __launch_bounds__(BNT) k_bwd_zero(const TileDesc* __restrict__ tiles, const LargeSeg* __restrict__ lsegs,
+                                                  const int32_t* __restrict__ seg_maxid, unsigned long long* acc,
+                                                  int32_t* cnt) {
+    const TileDesc td = tiles[blockIdx.x];
+    const LargeSeg ls = lsegs[td.lseg];
+    const int64_t slot0 = ls.kpos + td.lseg;
+    const int64_t r0 = (int64_t)td.tin * BTILE;
+    const int64_t r1 = min(r0 + BTILE, (int64_t)seg_maxid[td.lseg] + 1);
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += BNT) {
+        acc[2 * (slot0 + r)] = 0ull;
+        acc[2 * (slot0 + r) + 1] = 0ull;
+        cnt[slot0 + r] = 0;
+    }
+}
+
+// 3. exact cluster sums
+template <typename T>
+__global__ void __launch_bounds__(BNT) k_bwd_accum(const T* __restrict__ g, const int32_t* __restrict__ ids,
+                                                   const TileDesc* __restrict__ tiles,
+                                                   const LargeSeg* __restrict__ lsegs,
+                                                   const int32_t* __restrict__ seg_emax, unsigned long long* acc,
+                                                   int32_t* cnt) {
+    __shared__ long long wlo[BNT / 32], whi[BNT / 32];
+    __shared__ int wc[BNT / 32];
+    const TileDesc td = tiles[blockIdx.x];
+    const LargeSeg ls = lsegs[td.lseg];
+    const int64_t slot0 = ls.kpos + td.lseg;
+    const int emax = seg_emax[td.lseg];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    auto valid_id = [&](int id) { return id >= 0 && (int64_t)id < ls.len; };
+    // a tile whose elements all share one cluster adds its sum once
+    const int id0 = ids[td.vpos];
+    bool same = true;
+    for (int i = t; i < td.len; i += BNT) same &= ids[td.vpos + i] == id0;
+    if (__syncthreads_and(same)) {
+        if (!valid_id(id0)) return;
+        i128 s = 0;
+        for (int i = t; i < td.len; i += BNT) s += ws_bwd_fix<T>(g[td.vpos + i], emax);
+        s = ws_warp_reduce_i128(s);
+        if (lane == 0) { wlo[w] = (long long)(uint64_t)s; whi[w] = (long long)(uint64_t)((u128)s >> 64); }
+        __syncthreads();
+        if (t == 0) {
+            i128 tot = 0;
+            for (int k = 0; k < BNT / 32; ++k) tot += (i128)(((u128)(uint64_t)whi[k] << 64) | (u128)(uint64_t)wlo[k]);
+            ws_atomic_add_i128(acc + 2 * (slot0 + id0), tot);
+            atomicAdd(cnt + slot0 + id0, td.len);
+        }
+        return;
+    }
+    (void)wc;
+    // otherwise: lanes of a warp holding the same cluster add their sum once
+    for (int i0 = 0; i0 < td.len; i0 += BNT) {
+        const int i = i0 + t;
+        const bool in = i < td.len;
+        const int id = in ? ids[td.vpos + i] : -1;
+        const i128 q = in ? ws_bwd_fix<T>(g[td.vpos + i], emax) : (i128)0;
+        const unsigned peers = __match_any_sync(0xffffffffu, id);
+        const int leader = __ffs((int)peers) - 1;
+        i128 s = q;
+        if (__any_sync(0xffffffffu, __popc(peers) > 1)) {
+            // the leader gathers its group's values (every lane shuffles)
+            s = 0;
+            const long long qlo = (long long)(uint64_t)q, qhi = (long long)(uint64_t)((u128)q >> 64);
+            for (int src = 0; src < 32; ++src) {
+                const long long lo = __shfl_sync(0xffffffffu, qlo, src), hi = __shfl_sync(0xffffffffu, qhi, src);
+                if (lane == leader && ((peers >> src) & 1u)) s += (i128)(((u128)(uint64_t)hi << 64) | (u128)(uint64_t)lo);
+            }
+        }
+        if (in && lane == leader && valid_id(id)) {
+            ws_atomic_add_i128(acc + 2 * (slot0 + id), s);
+            atomicAdd(cnt + slot0 + id, __popc(peers));
+        }
+    }
+}
+
+// 4. cluster means (slots 0 .. max id of each segment)
+template <typename T>
+__global__ void __launch_bounds__(BNT) k_bwd_mean(const TileDesc* __restrict__ tiles, const LargeSeg* __restrict__ lsegs,
+                                                  const int32_t* __restrict__ seg_maxid,
+                                                  const int32_t* __restrict__ seg_emax,
+                                                  const unsigned long long* __restrict__ acc,
+                                                  const int32_t* __restrict__ cnt, T* mean) {
+    const TileDesc td = tiles[blockIdx.x];
+    const LargeSeg ls = lsegs[td.lseg];
+    const int64_t slot0 = ls.kpos + td.lseg;
+    const int64_t r0 = (int64_t)td.tin * BTILE;
+    const int64_t r1 = min(r0 + BTILE, (int64_t)seg_maxid[td.lseg] + 1);
+    const int emax = seg_emax[td.lseg];
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += BNT) {
+        const int c = cnt[slot0 + r];
+        if (c == 0) continue;
+        const i128 S = (i128)(((u128)acc[2 * (slot0 + r) + 1] << 64) | (u128)acc[2 * (slot0 + r)]);
+        mean[slot0 + r] = ws_bwd_mean<T>(S, c, emax);
+    }
+}
+
+// 5. every element takes its cluster's mean
+template <typename T>
+__global__ void __launch_bounds__(BNT) k_bwd_apply(const int32_t* __restrict__ ids, const TileDesc* __restrict__ tiles,
+                                                   const LargeSeg* __restrict__ lsegs, const T* __restrict__ mean,
+                                                   T* gin) {
+    const TileDesc td = tiles[blockIdx.x];
+    const LargeSeg ls = lsegs[td.lseg];
+    const int64_t slot0 = ls.kpos + td.lseg;
+    for (int i = threadIdx.x; i < td.len; i += BNT) {
+        const int id = ids[td.vpos + i];
+        if (id < 0 || (int64_t)id >= ls.len) continue;
+        gin[td.vpos + i] = mean[slot0 + id];
+    }
+}
+
+// One-CTA segments: the same exact sums in shared memory.
+template <typename T, int NT, int CAP>
+__global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, const int32_t* __restrict__ ids,
+                                                       const int64_t* __restrict__ offsets,
+                                                       const int32_t* __restrict__ seg_list, T* gin,
+                                                       uint32_t* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);   // [CAP][2]
+    int* cnt = reinterpret_cast<int*>(acc + 2 * CAP);                            // [CAP]
+    __shared__ int s_emax;
+    const int seg = seg_list[blockIdx.x];
+    const int64_t a0 = offsets[seg];
+    const int n = (int)(offsets[seg + 1] - a0);
+    if (n <= 0) return;
+    if (n > CAP) { if (threadIdx.x == 0) ws_flag(status, WS_STATUS_INTERNAL); return; }
+    if (threadIdx.x == 0) s_emax = 0;
+    int e = 0;
+    for (int i = threadIdx.x; i < n; i += NT) {
+        acc[2 * i] = 0ull;
+        acc[2 * i + 1] = 0ull;
+        cnt[i] = 0;
+        e = max(e, ws_g_exp(g[a0 + i]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicMax(&s_emax, e);
+    __syncthreads();
+    const int emax = s_emax;
+    for (int i = threadIdx.x; i < n; i += NT) {
+        const int id = ids[a0 + i];
+        if (id < 0 || id >= n) { ws_flag(status, WS_STATUS_INTERNAL); continue; }
+        ws_atomic_add_i128(acc + 2 * id, ws_bwd_fix<T>(g[a0 + i], emax));
+        atomicAdd(cnt + id, 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += NT) {
+        const int id = ids[a0 + i];
+        if (id < 0 || id >= n) continue;
+        const i128 S = (i128)(((u128)acc[2 * id + 1] << 64) | (u128)acc[2 * id]);
+        gin[a0 + i] = ws_bwd_mean<T>(S, cnt[id], emax);
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* ids, T* gin, uint32_t* status,
+                              cudaStream_t st) {
+    if (W.n_lseg == 0) return cudaSuccess;
+    // seg_emax / seg_maxid live in the backward's per-segment words
+    int32_t* seg_emax = W.bwd_seg;
+    int32_t* seg_maxid = W.bwd_seg + W.n_lseg;
+    cudaError_t e = cudaMemsetAsync(seg_emax, 0, sizeof(int32_t) * W.n_lseg, st);
+    if (e) return e;
+    e = cudaMemsetAsync(seg_maxid, 0xff, sizeof(int32_t) * W.n_lseg, st);
+    if (e) return e;
+    const int nt = W.n_sort_tiles;
+    WS_LAUNCH(W.prof, WSK_BWD, st,
+              (k_bwd_prep<T><<<nt, BNT, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, seg_maxid, status)));
+    WS_LAUNCH(W.prof, WSK_BWD, st, (k_bwd_zero<<<nt, BNT, 0, st>>>(W.sort_tiles, W.lsegs, seg_maxid, W.bacc, W.bcnt)));
+    WS_LAUNCH(W.prof, WSK_BWD, st,
+              (k_bwd_accum<T><<<nt, BNT, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, W.bacc, W.bcnt)));
+    WS_LAUNCH(W.prof, WSK_BWD, st,
+              (k_bwd_mean<T><<<nt, BNT, 0, st>>>(W.sort_tiles, W.lsegs, seg_maxid, seg_emax, W.bacc, W.bcnt,
+                                                 W.bsum)));
+    WS_LAUNCH(W.prof, WSK_BWD, st, (k_bwd_apply<T><<<nt, BNT, 0, st>>>(ids, W.sort_tiles, W.lsegs, W.bsum, gin)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64_t* offsets, const int32_t* seg_list,
+                                     int n_list, T* gin, uint32_t* status, cudaStream_t st, WsProf* prof) {
+    constexpr int NT = 256;
+    constexpr int CAP = SmallCfg<T>::CAP;
+    if (n_list <= 0) return cudaSuccess;
+    const size_t smem = (size_t)CAP * (2 * sizeof(unsigned long long) + sizeof(int));
+    auto k = k_small_backward<T, NT, CAP>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    WS_LAUNCH(prof, WSK_BWD, st, (k<<<n_list, NT, smem, st>>>(g, ids, offsets, seg_list, gin, status)));
+    return cudaGetLastError();
+}
+
+template cudaError_t ws_large_backward<float>(const LargeWork<float>&, const float*, const int32_t*, float*,
+                                              uint32_t*, cudaStream_t);
+template cudaError_t ws_large_backward<double>(const LargeWork<double>&, const double*, const int32_t*, double*,
+                                               uint32_t*, cudaStream_t);
+template cudaError_t ws_launch_small_backward<float>(const float*, const int32_t*, const int64_t*, const int32_t*,
+                                                     int, float*, uint32_t*, cudaStream_t, WsProf*);
+template cudaError_t ws_launch_small_backward<double>(const double*, const int32_t*, const int64_t*,
+                                                      const int32_t*, int, double*, uint32_t*, cudaStream_t,
+                                                      WsProf*);

@@ -165,8 +165,10 @@ struct LargeWork {
     CEntry<T>* table;        // [n_keys + n_lseg]
     DirEntry* dir;           // directory slices
     // backward
-    T* bsum;                 // [n_keys + n_lseg]
-    int32_t* bcnt;           // [n_keys + n_lseg]
+    T* bsum;                 // [n_keys + n_lseg] cluster means
+    int32_t* bcnt;           // [n_keys + n_lseg] cluster sizes
+    unsigned long long* bacc;   // [n_keys + n_lseg][2] exact cluster sums (128-bit, low word first)
+    int32_t* bwd_seg;        // [2 n_lseg] per segment: largest grad exponent, largest cluster id
     WsProf* prof;            // host-side launch accounting
 };
 

@@ -937,39 +937,6 @@ __global__ void __launch_bounds__(256) k_lookup(const T* __restrict__ values, co
     }
 }
 
-// ---------------------------------------------------------------------------
-// backward: per-cluster mean of grad_out (atomics into the cluster slots)
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_accum(const T* __restrict__ g, const int32_t* __restrict__ ids,
-                                                   const TileDesc* __restrict__ tiles,
-                                                   const LargeSeg* __restrict__ lsegs, T* bsum, int32_t* bcnt,
-                                                   uint32_t* status) {
-    const TileDesc td = tiles[blockIdx.x];
-    const LargeSeg ls = lsegs[td.lseg];
-    const int64_t slot0 = ls.kpos + td.lseg;
-    for (int i = threadIdx.x; i < td.len; i += 256) {
-        int id = ids[td.vpos + i];
-        if (id < 0 || id >= ls.len) { ws_flag(status, WS_STATUS_INTERNAL); continue; }
-        atomicAdd(&bsum[slot0 + id], g[td.vpos + i]);
-        atomicAdd(&bcnt[slot0 + id], 1);
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_apply(const int32_t* __restrict__ ids, const TileDesc* __restrict__ tiles,
-                                                   const LargeSeg* __restrict__ lsegs, const T* __restrict__ bsum,
-                                                   const int32_t* __restrict__ bcnt, T* gin) {
-    const TileDesc td = tiles[blockIdx.x];
-    const LargeSeg ls = lsegs[td.lseg];
-    const int64_t slot0 = ls.kpos + td.lseg;
-    for (int i = threadIdx.x; i < td.len; i += 256) {
-        int id = ids[td.vpos + i];
-        if (id < 0 || id >= ls.len) continue;
-        gin[td.vpos + i] = bsum[slot0 + id] / (T)bcnt[slot0 + id];
-    }
-}
-
 template <typename T>
 __global__ void k_copy_sorted(const typename KeyOf<T>::K* __restrict__ sorted, const TileDesc* __restrict__ tiles,
                               T* dst) {
@@ -1034,22 +1001,6 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
 }
 
 template <typename T>
-cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* ids, T* gin, uint32_t* status,
-                              cudaStream_t st) {
-    if (W.n_lseg == 0) return cudaSuccess;
-    size_t slots = (size_t)(W.n_keys + W.n_lseg);
-    cudaError_t e = cudaMemsetAsync(W.bsum, 0, sizeof(T) * slots, st);
-    if (e) return e;
-    e = cudaMemsetAsync(W.bcnt, 0, sizeof(int32_t) * slots, st);
-    if (e) return e;
-    WS_LAUNCH(W.prof, WSK_BWD, st,
-              (k_bwd_accum<T><<<W.n_sort_tiles, 256, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, W.bsum, W.bcnt, status)));
-    WS_LAUNCH(W.prof, WSK_BWD, st,
-              (k_bwd_apply<T><<<W.n_sort_tiles, 256, 0, st>>>(ids, W.sort_tiles, W.lsegs, W.bsum, W.bcnt, gin)));
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t ws_large_copy_sorted(const LargeWork<T>& W, const typename KeyOf<T>::K* sorted, T* dst,
                                  cudaStream_t st) {
     if (W.n_sort_tiles == 0) return cudaSuccess;
@@ -1060,8 +1011,6 @@ cudaError_t ws_large_copy_sorted(const LargeWork<T>& W, const typename KeyOf<T>:
 #define WS_INST(T)                                                                                                  \
     template cudaError_t ws_large_prox<T>(const LargeWork<T>&, const T*, const double*, T*, int32_t*, int64_t*, int, \
                                           const WsEpi&, uint32_t*, uint64_t, int, cudaStream_t);                    \
-    template cudaError_t ws_large_backward<T>(const LargeWork<T>&, const T*, const int32_t*, T*, uint32_t*,         \
-                                              cudaStream_t);                                                        \
     template cudaError_t ws_large_copy_sorted<T>(const LargeWork<T>&, const typename KeyOf<T>::K*, T*, cudaStream_t);
 WS_INST(float)
 WS_INST(double)

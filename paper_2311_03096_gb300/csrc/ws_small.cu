@@ -658,34 +658,6 @@ __global__ void __launch_bounds__(wsh::NT, 3) k_small(const T* __restrict__ valu
     if (t == 0 && n_clusters) n_clusters[seg] = C;
 }
 
-// Backward for short segments: per-cluster mean of grad_out (shared-memory sums).
-template <typename T, int NT, int CAP>
-__global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, const int32_t* __restrict__ ids,
-                                                       const int64_t* __restrict__ offsets,
-                                                       const int32_t* __restrict__ seg_list, T* gin,
-                                                       uint32_t* status) {
-    __shared__ T sum[CAP];
-    __shared__ int cnt[CAP];
-    const int seg = seg_list[blockIdx.x];
-    const int64_t a0 = offsets[seg];
-    const int n = (int)(offsets[seg + 1] - a0);
-    if (n <= 0) return;
-    if (n > CAP) { if (threadIdx.x == 0) ws_flag(status, WS_STATUS_INTERNAL); return; }
-    for (int i = threadIdx.x; i < n; i += NT) { sum[i] = (T)0; cnt[i] = 0; }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += NT) {
-        int id = ids[a0 + i];
-        if (id < 0 || id >= n) { ws_flag(status, WS_STATUS_INTERNAL); continue; }
-        atomicAdd(&sum[id], g[a0 + i]);
-        atomicAdd(&cnt[id], 1);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += NT) {
-        int id = ids[a0 + i];
-        if (id >= 0 && id < n) gin[a0 + i] = sum[id] / (T)cnt[id];
-    }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -719,23 +691,9 @@ cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64_t* offsets, const int32_t* seg_list,
-                                     int n_list, T* gin, uint32_t* status, cudaStream_t st, WsProf* prof) {
-    constexpr int NT = 256;
-    if (n_list <= 0) return cudaSuccess;
-    WS_LAUNCH(prof, WSK_BWD, st,
-              (k_small_backward<T, NT, SmallCfg<T>::CAP><<<n_list, NT, 0, st>>>(g, ids, offsets, seg_list, gin, status)));
-    return cudaGetLastError();
-}
-
 template cudaError_t ws_launch_small<float>(const float*, const int64_t*, const int32_t*, int, const double*, float*,
                                             int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t, WsProf*,
                                             int32_t*, int32_t*, int);
 template cudaError_t ws_launch_small<double>(const double*, const int64_t*, const int32_t*, int, const double*,
                                              double*, int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t,
                                              WsProf*, int32_t*, int32_t*, int);
-template cudaError_t ws_launch_small_backward<float>(const float*, const int32_t*, const int64_t*, const int32_t*,
-                                                     int, float*, uint32_t*, cudaStream_t, WsProf*);
-template cudaError_t ws_launch_small_backward<double>(const double*, const int32_t*, const int64_t*,
-                                                      const int32_t*, int, double*, uint32_t*, cudaStream_t, WsProf*);
