@@ -279,6 +279,12 @@ def bench_batched(ws, ctx, stream, peak, reps=5):
         entry = {"elements": int(sub_off[-1]), "segments": int(len(idx)), "ms": ms,
                  "elements_per_s": sub_off[-1] / (ms / 1e3), "elements_one_cta": e_small,
                  **byte_fracs(e_small, e_large, ms, peak)}
+        if name == "rows":
+            g_r = torch.from_numpy(inputs.normal(int(sub_off[-1]), seed=5, dtype=np.float32)).to(dev)
+            gin_r = torch.empty_like(g_r)
+            entry["backward_ms"] = _time_calls(lambda: plan.backward(g_r, ids, grad_in=gin_r, stream=stream), stream,
+                                               reps)
+            del g_r, gin_r
         if name == "all":
             g = torch.cuda.CUDAGraph()
             side = torch.cuda.Stream()
@@ -598,6 +604,35 @@ def main():
                 torch.cuda.synchronize()
                 variants[f"f32_{prec}_lam{lam:g}"] = {"elements_per_s": args.d * reps / (a.elapsed_time(b) / 1e3),
                                                       "clusters": int(nc.item())}
+        # the cluster merge path of each lambda: in-tile Imminent Collisions
+        # rounds (default round cap) against the tree of bridge merges alone
+        # (cap 0), and which path every hull tile took
+        merge_paths = {}
+        for lam in LAMBDAS:
+            entry = {}
+            for name, cap in (("ic_rounds", -1), ("merges_only", 0)):
+                ctx.set_ic_cap(cap)
+                ws.prox(w, lam, args.prec, ctx=ctx, out=out, n_clusters=nc)
+                ms = _time_calls(lambda: ws.prox(w, lam, args.prec, ctx=ctx, out=out, n_clusters=nc), stream, 10)
+                hs = ctx.hull_stats(args.d)
+                entry[name] = {"ms_per_step": ms, "tiles_general_kernel": hs["general"],
+                               "tiles_capped_to_merges": hs["capped"],
+                               "tiles_converged_by_rounds": {str(r): c for r, c in enumerate(hs["rounds"]) if r and c}}
+            ctx.set_ic_cap(-1)
+            merge_paths[f"lam{lam:g}"] = entry
+        variants["merge_paths"] = merge_paths
+        # backward (cluster-mean Jacobian), exact fixed-point sums
+        g_t = torch.from_numpy(inputs.normal(args.d, seed=args.seed + 1, dtype=np.float32)).to(dev)
+        gin_t = torch.empty_like(g_t)
+        bwd = {}
+        for lam in LAMBDAS:
+            _, ids_l, _ = ws.prox(w, lam, args.prec, ctx=ctx)
+            ms = _time_calls(lambda: ws.prox_backward(g_t, ids_l, ctx=ctx, grad_in=gin_t), stream, 5)
+            bwd[f"lam{lam:g}"] = {"ms": ms, "elements_per_s": args.d / (ms / 1e3)}
+            del ids_l
+        variants["backward_single_vector"] = bwd
+        del g_t, gin_t
+        ctx.check(what="bench merge paths")
         w64 = w.double()
         out64 = torch.empty_like(w64)
         for lam in LAMBDAS:

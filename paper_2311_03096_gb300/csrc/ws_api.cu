@@ -73,7 +73,8 @@ struct ws_plan {
     Piece* pieces = nullptr;
     int32_t* npieces = nullptr;
     int32_t* tile_piece = nullptr;
-    int32_t* tile_general = nullptr;
+    int32_t* gen_list = nullptr;
+    int32_t* gen_count = nullptr;
     int32_t* keepR = nullptr;
     int32_t* keepL = nullptr;
     int32_t* jflag0 = nullptr;
@@ -121,7 +122,8 @@ LargeWork<T> make_work(const ws_plan* p) {
     W.pieces = p->pieces;
     W.npieces = p->npieces;
     W.tile_piece = p->tile_piece;
-    W.tile_general = p->tile_general;
+    W.gen_list = p->gen_list;
+    W.gen_count = p->gen_count;
     W.keepR = p->keepR;
     W.keepL = p->keepL;
     W.jflag0 = p->jflag0;
@@ -251,7 +253,8 @@ ws_status build_plan(ws_plan* p) {
     if ((st = plan_alloc(p, (void**)&p->pieces, sizeof(Piece) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->npieces, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->tile_piece, sizeof(int32_t) * nh))) return st;
-    if ((st = plan_alloc(p, (void**)&p->tile_general, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->gen_list, sizeof(int32_t) * nh))) return st;
+    if ((st = plan_alloc(p, (void**)&p->gen_count, sizeof(int32_t)))) return st;
     if ((st = plan_alloc(p, (void**)&p->keepR, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->keepL, sizeof(int32_t) * nh))) return st;
     if ((st = plan_alloc(p, (void**)&p->jflag0, sizeof(int32_t) * nh))) return st;

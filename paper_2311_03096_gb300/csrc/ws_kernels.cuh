@@ -150,7 +150,8 @@ struct LargeWork {
     Piece* pieces;           // [n_hull_tiles]
     int32_t* npieces;        // [n_hull_tiles] pieces of the node whose first tile is this index
     int32_t* tile_piece;     // [n_hull_tiles] piece index in the root list or -1
-    int32_t* tile_general;   // [n_hull_tiles] 1: the tile's hull comes from the general kernel
+    int32_t* gen_list;       // [n_hull_tiles] tiles whose hull the general kernel builds
+    int32_t* gen_count;      // [1] their number
     int32_t* keepR;          // [n_hull_tiles] junction results (ws_tile.cu)
     int32_t* keepL;          // [n_hull_tiles]
     int32_t* jflag0;         // [n_hull_tiles]

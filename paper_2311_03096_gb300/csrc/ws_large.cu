@@ -477,23 +477,26 @@ struct TileHullSmem {
 
 // The general tile kernel: the exact hull of a tile whose prefix sums need
 // 128 bits (or whose bridge walks were too long for the lean kernel of
-// ws_tile.cu, which flags such tiles in tile_general).  Other tiles exit at
-// once.  Four CTAs per SM (64 registers; only the rare merge paths spill).
+// ws_tile.cu, which lists such tiles in gen_list).  A small grid walks the
+// list.  Four CTAs per SM (64 registers; only the rare merge paths spill).
 template <typename T>
 __global__ void __launch_bounds__(HNT, 4) k_tile_hull(const typename KeyOf<T>::K* __restrict__ sorted,
                                                    const TileDesc* __restrict__ htiles,
                                                    const LargeSeg* __restrict__ lsegs,
                                                    const double* __restrict__ lambdas, SegRuntime* rt,
                                                    uint16_t* vp, i128* vx, int32_t* nvert, i128* tile_total,
-                                                   const int32_t* __restrict__ tile_general,
+                                                   const int32_t* __restrict__ gen_list,
+                                                   const int32_t* __restrict__ gen_count,
                                                    const int32_t* __restrict__ seg_emin, uint32_t* status) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileHullSmem& s = *reinterpret_cast<TileHullSmem*>(smem_raw);
     const int t = threadIdx.x;
-    const int tile = blockIdx.x;
-    if (!tile_general[tile]) return;
+    const int n_list = *gen_count;
+    for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+    __syncthreads();   // (the previous tile's shared memory is dead)
+    const int tile = gen_list[li];
     const TileDesc td = htiles[tile];
     const LargeSeg ls = lsegs[td.lseg];
     const double lam = lambdas[ls.seg];
@@ -579,14 +582,16 @@ __global__ void __launch_bounds__(HNT, 4) k_tile_hull(const typename KeyOf<T>::K
         nvert[tile] = nv;
         __stcg(reinterpret_cast<uint4*>(tile_total + tile), *reinterpret_cast<const uint4*>(&total));
     }
+    }
 }
 
 // ---------------------------------------------------------------------------
 // 3. the tree of bridge merges across tiles, for segments whose junctions do
-// not resolve locally (seg_mode 2).  One CTA per hull tile; all tile hulls
-// are written.  Each CTA starts its tile's node list, then climbs: at each
-// level the CTA that arrives second merges the two children of the parent;
-// the first one exits.  Nobody waits.
+// not resolve locally (seg_mode 2).  All tile hulls are written.  A CTA takes
+// one hull tile after another (a small grid); for each it starts the tile's
+// node list, then climbs: at each level the CTA that arrives second merges
+// the two children of the parent, the first one goes on to its next tile.
+// Nobody waits.
 // ---------------------------------------------------------------------------
 constexpr int CLIMB_CACHE = 1024;   // piece lists up to this long are searched from shared memory
 
@@ -606,9 +611,10 @@ __global__ void __launch_bounds__(HNT) k_climb(const TileDesc* __restrict__ htil
                                                const int32_t* __restrict__ seg_mode) {
     __shared__ ClimbSmem s;
     const int t = threadIdx.x;
-    const int tile = blockIdx.x;
+    for (int tile = blockIdx.x; tile < n_hull; tile += gridDim.x) {
     const TileDesc td = htiles[tile];
-    if (seg_mode[td.lseg] != 2) return;
+    if (seg_mode[td.lseg] != 2) continue;   // (uniform)
+    __syncthreads();   // (the previous tile's shared memory is dead)
     const LargeSeg ls = lsegs[td.lseg];
     if (t == 0) {
         double lam = lambdas[ls.seg];
@@ -637,6 +643,7 @@ __global__ void __launch_bounds__(HNT) k_climb(const TileDesc* __restrict__ htil
         if (!s.go) break;
         ws_merge_children(s.ms, pieces, npieces, tile_total, ls.hull_first + parent_base, ls.hull_first + right_base,
                           vp, vx, ls.hull_first, s.sc, s.cache, CLIMB_CACHE);
+    }
     }
 }
 
@@ -964,10 +971,11 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
     size_t smem = sizeof(TileHullSmem);
     e = cudaFuncSetAttribute(k_tile_hull<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
+    const int small_grid = W.n_hull_tiles < 4 * 152 ? W.n_hull_tiles : 4 * 152;
     WS_LAUNCH(W.prof, WSK_TILE_GENERAL, st,
-              (k_tile_hull<T><<<W.n_hull_tiles, HNT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp,
-                                                                W.vx, W.nvert, W.tile_total, W.tile_general,
-                                                                W.seg_emin, status)));
+              (k_tile_hull<T><<<small_grid, HNT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp, W.vx,
+                                                            W.nvert, W.tile_total, W.gen_list, W.gen_count,
+                                                            W.seg_emin, status)));
     // across tiles: junction bridges and the per-segment resolution, then the
     // tree of merges for the segments that need it
     e = ws_large_junctions<T>(W, lambdas, st);
@@ -975,7 +983,7 @@ cudaError_t ws_large_prox(const LargeWork<T>& W, const T* values, const double* 
     e = cudaMemsetAsync(W.arrive, 0, sizeof(int32_t) * (size_t)n_levels * W.n_hull_tiles, st);
     if (e) return e;
     WS_LAUNCH(W.prof, WSK_CLIMB, st,
-              (k_climb<T><<<W.n_hull_tiles, HNT, 0, st>>>(W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp, W.vx, W.nvert,
+              (k_climb<T><<<small_grid, HNT, 0, st>>>(W.hull_tiles, W.lsegs, lambdas, W.rt, W.vp, W.vx, W.nvert,
                                                           W.tile_total, W.pieces, W.npieces, W.arrive,
                                                           W.n_hull_tiles, W.seg_mode)));
     e = cudaMemsetAsync(W.tile_piece, 0xff, sizeof(int32_t) * (size_t)W.n_hull_tiles, st);

@@ -6,7 +6,7 @@
 //   k_hull_fast  builds each tile's exact lower hull (ws_hull.cuh) and writes
 //                its vertices (tile-local point, fixed-point prefix X);
 //                tiles whose prefix sums do not fit the 64-bit lean path are
-//                flagged and built by the general tile kernel (ws_large.cu).
+//                listed for the general tile kernel (ws_large.cu).
 //   k_junction   finds the bridge (common lower tangent) between the hulls of
 //                tiles T and T+1 for every junction, one thread each.
 //   k_resolve    per segment: if every tile keeps at least two vertices
@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
                                                    const LargeSeg* __restrict__ lsegs,
                                                    const SegRuntime* __restrict__ rt,
                                                    const TileScale* __restrict__ scales, uint16_t* vp, i128* vx,
-                                                   int32_t* nvert, i128* tile_total, int32_t* tile_general,
-                                                   int32_t* tile_rounds, int ic_cap) {
+                                                   int32_t* nvert, i128* tile_total, int32_t* gen_list,
+                                                   int32_t* gen_count, int32_t* tile_rounds, int ic_cap) {
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -121,8 +121,7 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
     const bool lean = ws_lean_x(range, n);   // prefix sums in 64 bits
     const bool d64 = ws_lean_tile(range, n);  // every Delta too
     if (t == 0) {
-        tile_general[tile] = lean ? 0 : 1;
-        if (!lean) tile_rounds[tile] = -2;
+        if (!lean) { gen_list[atomicAdd(gen_count, 1)] = tile; tile_rounds[tile] = -2; }
         else S.ts = scales[(size_t)td.lseg * WS_NSCALE + (bin ? sh : WS_NSCALE - 1)];
         s.general = 0;
     }
@@ -199,7 +198,7 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
         c = __popc(B) + (t == 0 ? 1 : 0) + (first < n && last == n ? 1 : 0);
     } else {
         if (!wsh::chain_tree_hull(s, tst, t, first, last, n, Xf, CTA_WALK_CAP)) {
-            if (t == 0) { tile_general[tile] = 1; tile_rounds[tile] = -2; }
+            if (t == 0) { gen_list[atomicAdd(gen_count, 1)] = tile; tile_rounds[tile] = -2; }
             return;
         }
         lo = s.lo[t];
@@ -478,9 +477,11 @@ cudaError_t ws_large_hull_fast(const LargeWork<T>& W, const typename KeyOf<T>::K
     const size_t smem = sizeof(FastSmem);
     cudaError_t e = cudaFuncSetAttribute(k_hull_fast<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
+    e = cudaMemsetAsync(W.gen_count, 0, sizeof(int32_t), st);
+    if (e) return e;
     WS_LAUNCH(W.prof, WSK_TILE_HULL, st,
               (k_hull_fast<T><<<W.n_hull_tiles, NT, smem, st>>>(sorted, W.hull_tiles, W.lsegs, W.rt, W.scales, W.vp,
-                                                                W.vx, W.nvert, W.tile_total, W.tile_general,
+                                                                W.vx, W.nvert, W.tile_total, W.gen_list, W.gen_count,
                                                                 W.tile_rounds, W.ic_cap)));
     return cudaGetLastError();
 }
