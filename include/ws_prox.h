@@ -213,7 +213,7 @@ void ws_debug_set_spin_limit(ws_ctx* ctx, int64_t limit);
 /* Segments no longer than `small_max` elements go to the fused single-CTA
  * kernel, longer ones to the device-wide path.  Applies to plans created
  * afterwards (cached single-vector plans are dropped); a negative value
- * restores the default (4096 for float, 2048 for double, also the maximum).
+ * restores the default (4096 for float and double, also the maximum).
  * Test hook: lets small inputs exercise the device-wide path. */
 void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max);
 

@@ -62,6 +62,23 @@ __device__ __forceinline__ void ws_atomic_add_i128(unsigned long long* lo_hi, i1
 
 template <typename T> __device__ __forceinline__ int ws_g_exp(T g) { return g != (T)0 ? ws_eff_exp(g) : 0; }
 
+// Sum of v over the lanes in `peers` (every one of them calls with the same
+// mask; the groups of a __match_any_sync may call side by side).  |v| < 2^95
+// (a ws_bwd_fix value), so v + 2^95 lies in [0, 2^96): its four 24-bit limbs
+// are summed separately -- at most 32 * (2^24 - 1) < 2^29 each, no carry is
+// lost -- and recombined.  Exact.
+__device__ __forceinline__ i128 ws_group_sum_i96(unsigned peers, i128 v) {
+    const u128 o = (u128)(v + ((i128)1 << 95));
+    const uint32_t lo = (uint32_t)(uint64_t)o, mid = (uint32_t)(uint64_t)(o >> 32),
+                   hi = (uint32_t)(uint64_t)(o >> 64);
+    const uint32_t s0 = __reduce_add_sync(peers, lo & 0xffffffu);
+    const uint32_t s1 = __reduce_add_sync(peers, (lo >> 24) | ((mid & 0xffffu) << 8));
+    const uint32_t s2 = __reduce_add_sync(peers, (mid >> 16) | ((hi & 0xffu) << 16));
+    const uint32_t s3 = __reduce_add_sync(peers, hi >> 8);
+    const u128 S = (u128)s0 + ((u128)s1 << 24) + ((u128)s2 << 48) + ((u128)s3 << 72);
+    return (i128)S - (i128)__popc(peers) * ((i128)1 << 95);
+}
+
 // 1. per segment: largest exponent of grad_out and largest cluster id
 template <typename T>
 __global__ void __launch_bounds__(BNT) k_bwd_prep(const T* __restrict__ g, const int32_t* __restrict__ ids,
@@ -115,7 +132,6 @@ __global__ void __launch_bounds__(BNT) k_bwd_accum(const T* __restrict__ g, cons
                                                    const int32_t* __restrict__ seg_emax, unsigned long long* acc,
                                                    int32_t* cnt) {
     __shared__ long long wlo[BNT / 32], whi[BNT / 32];
-    __shared__ int wc[BNT / 32];
     const TileDesc td = tiles[blockIdx.x];
     const LargeSeg ls = lsegs[td.lseg];
     const int64_t slot0 = ls.kpos + td.lseg;
@@ -141,7 +157,6 @@ __global__ void __launch_bounds__(BNT) k_bwd_accum(const T* __restrict__ g, cons
         }
         return;
     }
-    (void)wc;
     // otherwise: lanes of a warp holding the same cluster add their sum once
     for (int i0 = 0; i0 < td.len; i0 += BNT) {
         const int i = i0 + t;
@@ -150,16 +165,7 @@ __global__ void __launch_bounds__(BNT) k_bwd_accum(const T* __restrict__ g, cons
         const i128 q = in ? ws_bwd_fix<T>(g[td.vpos + i], emax) : (i128)0;
         const unsigned peers = __match_any_sync(0xffffffffu, id);
         const int leader = __ffs((int)peers) - 1;
-        i128 s = q;
-        if (__any_sync(0xffffffffu, __popc(peers) > 1)) {
-            // the leader gathers its group's values (every lane shuffles)
-            s = 0;
-            const long long qlo = (long long)(uint64_t)q, qhi = (long long)(uint64_t)((u128)q >> 64);
-            for (int src = 0; src < 32; ++src) {
-                const long long lo = __shfl_sync(0xffffffffu, qlo, src), hi = __shfl_sync(0xffffffffu, qhi, src);
-                if (lane == leader && ((peers >> src) & 1u)) s += (i128)(((u128)(uint64_t)hi << 64) | (u128)(uint64_t)lo);
-            }
-        }
+        const i128 s = __any_sync(0xffffffffu, __popc(peers) > 1) ? ws_group_sum_i96(peers, q) : q;
         if (in && lane == leader && valid_id(id)) {
             ws_atomic_add_i128(acc + 2 * (slot0 + id), s);
             atomicAdd(cnt + slot0 + id, __popc(peers));
@@ -203,12 +209,16 @@ __global__ void __launch_bounds__(BNT) k_bwd_apply(const int32_t* __restrict__ i
     }
 }
 
-// One-CTA segments: the same exact sums in shared memory.
+// One-CTA segments: the same exact sums in shared memory.  Every thread keeps
+// its CAP / NT elements (grad_out and id) in registers; lanes of a warp with
+// the same cluster add once; each used slot forms its mean once, in place.
 template <typename T, int NT, int CAP>
 __global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, const int32_t* __restrict__ ids,
                                                        const int64_t* __restrict__ offsets,
                                                        const int32_t* __restrict__ seg_list, T* gin,
                                                        uint32_t* status) {
+    constexpr int PER = CAP / NT;
+    static_assert(CAP % NT == 0, "whole elements per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem_raw);   // [CAP][2]
     int* cnt = reinterpret_cast<int*>(acc + 2 * CAP);                            // [CAP]
@@ -218,32 +228,58 @@ __global__ void __launch_bounds__(NT) k_small_backward(const T* __restrict__ g, 
     const int n = (int)(offsets[seg + 1] - a0);
     if (n <= 0) return;
     if (n > CAP) { if (threadIdx.x == 0) ws_flag(status, WS_STATUS_INTERNAL); return; }
-    if (threadIdx.x == 0) s_emax = 0;
+    const int t = threadIdx.x, lane = t & 31;
+    if (t == 0) s_emax = 0;
+    T gv[PER];
+    int idv[PER];
     int e = 0;
-    for (int i = threadIdx.x; i < n; i += NT) {
-        acc[2 * i] = 0ull;
-        acc[2 * i + 1] = 0ull;
-        cnt[i] = 0;
-        e = max(e, ws_g_exp(g[a0 + i]));
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = t + k * NT;
+        gv[k] = (T)0;
+        idv[k] = -1;
+        if (i < n) {
+            gv[k] = g[a0 + i];
+            const int id = ids[a0 + i];
+            if (id >= 0 && id < n) idv[k] = id; else bad = true;
+            acc[2 * i] = 0ull;
+            acc[2 * i + 1] = 0ull;
+            cnt[i] = 0;
+        }
+        e = max(e, ws_g_exp(gv[k]));
     }
+    if (bad) ws_flag(status, WS_STATUS_INTERNAL);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) atomicMax(&s_emax, e);
+    if (lane == 0) atomicMax(&s_emax, e);
     __syncthreads();
     const int emax = s_emax;
-    for (int i = threadIdx.x; i < n; i += NT) {
-        const int id = ids[a0 + i];
-        if (id < 0 || id >= n) { ws_flag(status, WS_STATUS_INTERNAL); continue; }
-        ws_atomic_add_i128(acc + 2 * id, ws_bwd_fix<T>(g[a0 + i], emax));
-        atomicAdd(cnt + id, 1);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int id = idv[k];
+        const i128 q = ws_bwd_fix<T>(gv[k], emax);
+        const unsigned peers = __match_any_sync(0xffffffffu, id);
+        const i128 s = __any_sync(0xffffffffu, __popc(peers) > 1) ? ws_group_sum_i96(peers, q) : q;
+        if (id >= 0 && lane == __ffs((int)peers) - 1) {
+            ws_atomic_add_i128(acc + 2 * id, s);
+            atomicAdd(cnt + id, __popc(peers));
+        }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += NT) {
-        const int id = ids[a0 + i];
-        if (id < 0 || id >= n) continue;
-        const i128 S = (i128)(((u128)acc[2 * id + 1] << 64) | (u128)acc[2 * id]);
-        gin[a0 + i] = ws_bwd_mean<T>(S, cnt[id], emax);
+    // the mean of slot r replaces its low word (only this thread touches slot r)
+    for (int r = t; r < n; r += NT) {
+        const int c = cnt[r];
+        if (c == 0) continue;
+        const i128 S = (i128)(((u128)acc[2 * r + 1] << 64) | (u128)acc[2 * r]);
+        *reinterpret_cast<T*>(acc + 2 * r) = ws_bwd_mean<T>(S, c, emax);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = t + k * NT;
+        if (i < n && idv[k] >= 0) gin[a0 + i] = *reinterpret_cast<const T*>(acc + 2 * idv[k]);
     }
 }
 

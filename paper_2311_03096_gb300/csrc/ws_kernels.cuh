@@ -5,7 +5,7 @@
 
 template <typename T> struct SmallCfg;
 template <> struct SmallCfg<float> { static constexpr int M = 16; static constexpr int CAP = 256 * 16; };
-template <> struct SmallCfg<double> { static constexpr int M = 8; static constexpr int CAP = 256 * 8; };
+template <> struct SmallCfg<double> { static constexpr int M = 16; static constexpr int CAP = 256 * 16; };
 
 // Opt-in per-launch timing (CUDA events recorded on the launching stream
 // around every kernel) and a launch counter.  Host-side only.

@@ -1,5 +1,5 @@
-// ws_small.cu -- fused single-CTA prox for short segments (n <= 4096 for
-// float, 2048 for double): one CTA loads a segment once, sorts (key, index)
+// ws_small.cu -- fused single-CTA prox for short segments (n <= 4096, float
+// and double): one CTA loads a segment once, sorts (key, index)
 // pairs in shared memory, builds the exact hull, and writes values and cluster
 // ids straight to their original positions.  HBM traffic is the I/O floor:
 // read w, write out and id (12 B/element for float).  The lean kernel
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(NT, 3) k_small_general(const T* __restrict__ v
 template <typename T>
 struct LeanSmem {
     typedef typename KeyOf<T>::K K;
-    static constexpr int CAP = 16384 / sizeof(K);       // 4096 (float), 2048 (double)
+    static constexpr int CAP = wsh::TILE;               // 4096 elements, float and double
     // Arrays read in blocks of 16 consecutive entries per thread are padded
     // (keys: one slot per 16, 16-bit arrays: two) so those reads do not
     // collide in the shared-memory banks; see kpad / ipad.
@@ -303,7 +303,7 @@ struct LeanSmem {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(wsh::NT, 3) k_small(const T* __restrict__ values,
+__global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const T* __restrict__ values,
                                                    const int64_t* __restrict__ offsets,
                                                    const int32_t* __restrict__ seg_list,
                                                    const double* __restrict__ lambdas, T* out, int32_t* ids,
