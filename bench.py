@@ -382,32 +382,40 @@ def bench_configs(ws, ctx, stream):
 
 
 def bench_train(ws, ctx, stream, steps=10):
-    """Proximal SGD step on the MLP (batch 256 of 32x32x3): ms per step and the prox share."""
+    """Proximal SGD step on the MLP (batch 256 of 32x32x3): ms per step and the
+    prox share, cold and with the warm start from the previous step's clusters."""
     import torch
 
     from paper_2311_03096_gb300 import inputs
     from paper_2311_03096_gb300.train import ProxMLP
 
-    m = ProxMLP(seed=0)
     x_np, y_np = inputs.images(batch=256, seed=0)
     x, y = torch.from_numpy(x_np).cuda(), torch.from_numpy(y_np).cuda()
-    for _ in range(3):
-        m.step(x, y)
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
-    for k in range(steps):
-        ev[3 * k].record(stream)
-        m.sgd(x, y)
-        ev[3 * k + 1].record(stream)
-        m.prox(stream=stream)
-        ev[3 * k + 2].record(stream)
-    torch.cuda.synchronize()
-    ctx.check(what="bench train")
-    step = sum(ev[3 * k].elapsed_time(ev[3 * k + 2]) for k in range(steps)) / steps
-    prox = sum(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(steps)) / steps
-    return {"ms_per_step": step, "prox_ms": prox, "prox_share": prox / step,
-            "rows": int(m.offsets.shape[0] - 1), "weights": int(m.flat.shape[0]), "batch": 256,
-            "lr": m.lr, "alpha": m.alpha}
+    res = {}
+    for warm in (False, True):
+        m = ProxMLP(seed=0, warm=warm)
+        for _ in range(3):
+            m.step(x, y)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * steps)]
+        for k in range(steps):
+            ev[3 * k].record(stream)
+            m.sgd(x, y)
+            ev[3 * k + 1].record(stream)
+            m.prox(stream=stream)
+            ev[3 * k + 2].record(stream)
+        torch.cuda.synchronize()
+        ctx.check(what="bench train")
+        step = sum(ev[3 * k].elapsed_time(ev[3 * k + 2]) for k in range(steps)) / steps
+        prox = sum(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(steps)) / steps
+        r = {"ms_per_step": step, "prox_ms": prox, "prox_share": prox / step}
+        if not warm:
+            res.update(r)
+            res.update({"rows": int(m.offsets.shape[0] - 1), "weights": int(m.flat.shape[0]), "batch": 256,
+                        "lr": m.lr, "alpha": m.alpha})
+        else:
+            res["warm_start"] = r
+    return res
 
 
 def config_dict(args, world):

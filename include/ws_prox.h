@@ -120,6 +120,22 @@ ws_status ws_plan_autotune(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, 
 ws_status ws_prox_batched(ws_plan* plan, const void* values, const double* lambdas, void* out,
                           int32_t* cluster_ids, int64_t* n_clusters, ws_prec prec, void* stream);
 
+/* Warm-started batched forward (the paper's Future Work: start from a
+ * candidate weight-sharing and edit it into the exact one).  ids_prev: n int32
+ * in DEVICE memory, the cluster ids of an earlier call on nearby values (the
+ * previous training step's cluster_ids); any values are accepted.  In every
+ * segment of the one-CTA kernel, the runs of equal ids_prev (low 16 bits)
+ * along the sorted order are the candidate: points that lie on or above the
+ * chord of their run cannot be hull vertices and are dropped before the
+ * Imminent Collisions rounds (Sec. 4) start.  Outputs are those of
+ * ws_prox_batched for ANY ids_prev -- it changes the time only.  ids_prev may
+ * alias cluster_ids (a segment reads it before writing); device-wide segments
+ * ignore it.  NULL ids_prev with n > 0 is WS_ERR_INVALID; other arguments as
+ * for ws_prox_batched. */
+ws_status ws_prox_batched_warm(ws_plan* plan, const void* values, const double* lambdas,
+                               const int32_t* ids_prev, void* out, int32_t* cluster_ids,
+                               int64_t* n_clusters, ws_prec prec, void* stream);
+
 /* Single vector of length d with a host lambda.  Plans (and allocates) on
  * first use of a given (d, dtype) and caches the plan in the context, so the
  * first call for a shape is not capturable; later calls are.  n_clusters is

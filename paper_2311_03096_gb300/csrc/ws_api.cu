@@ -286,11 +286,12 @@ ws_status map_cuda(cudaError_t e) {
 
 template <typename T>
 ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, void* out, int32_t* ids,
-                      int64_t* n_clusters, ws_prec prec, const WsEpi& ep, cudaStream_t st) {
+                      int64_t* n_clusters, ws_prec prec, const WsEpi& ep, cudaStream_t st,
+                      const int32_t* ids_prev = nullptr) {
     const int fp64 = prec == WS_PREC_FP64 ? 1 : 0;
     cudaError_t e = ws_launch_small<T>((const T*)values, p->d_offsets, p->d_small, p->n_small, lambdas, (T*)out, ids,
                                        n_clusters, fp64, ep, p->ctx->status, st, &p->ctx->prof, p->small_gen,
-                                       p->small_gen_count, p->ctx->ic_cap);
+                                       p->small_gen_count, p->ctx->ic_cap, ids_prev);
     if (e) return map_cuda(e);
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);
@@ -435,7 +436,8 @@ static ws_status make_epi(const ws_l1_rewind* epi, WsEpi* ep) {
 }
 
 static ws_status batched_impl(ws_plan* plan, const void* values, const double* lambdas, const ws_l1_rewind* epi, void* out,
-                       int32_t* cluster_ids, int64_t* n_clusters, ws_prec prec, void* stream) {
+                       int32_t* cluster_ids, int64_t* n_clusters, ws_prec prec, void* stream,
+                       const int32_t* ids_prev = nullptr) {
     if (!plan || (prec != WS_PREC_FP32_COMP && prec != WS_PREC_FP64)) return WS_ERR_INVALID;
     if (plan->n > 0 && (!values || !out)) return WS_ERR_INVALID;
     if (plan->n_seg > 0 && !lambdas) return WS_ERR_INVALID;
@@ -444,8 +446,8 @@ static ws_status batched_impl(ws_plan* plan, const void* values, const double* l
     if (plan->n_seg == 0) return WS_OK;
     cudaStream_t st = (cudaStream_t)stream;
     return plan->dtype == WS_F64
-               ? run_forward<double>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, ep, st)
-               : run_forward<float>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, ep, st);
+               ? run_forward<double>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, ep, st, ids_prev)
+               : run_forward<float>(plan, values, lambdas, out, cluster_ids, n_clusters, prec, ep, st, ids_prev);
 }
 
 static ws_status single_impl(ws_ctx* ctx, const void* w, int64_t d, double lambda, const ws_l1_rewind* epi, void* out,
@@ -468,6 +470,12 @@ static ws_status single_impl(ws_ctx* ctx, const void* w, int64_t d, double lambd
 ws_status ws_prox_batched(ws_plan* plan, const void* values, const double* lambdas, void* out, int32_t* cluster_ids,
                           int64_t* n_clusters, ws_prec prec, void* stream) {
     return batched_impl(plan, values, lambdas, nullptr, out, cluster_ids, n_clusters, prec, stream);
+}
+
+ws_status ws_prox_batched_warm(ws_plan* plan, const void* values, const double* lambdas, const int32_t* ids_prev,
+                               void* out, int32_t* cluster_ids, int64_t* n_clusters, ws_prec prec, void* stream) {
+    if (plan && plan->n > 0 && !ids_prev) return WS_ERR_INVALID;
+    return batched_impl(plan, values, lambdas, nullptr, out, cluster_ids, n_clusters, prec, stream, ids_prev);
 }
 
 ws_status ws_prox_batched_l1(ws_plan* plan, const void* values, const double* lambdas, const ws_l1_rewind* epi,

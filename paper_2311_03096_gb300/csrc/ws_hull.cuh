@@ -622,6 +622,56 @@ __device__ __forceinline__ bool ic_rounds(Smem& s, const Test& T, int t, int fir
     }
 }
 
+// Warm start from a candidate partition given as runs of points (the paper's
+// Future Work: start from a candidate weight-sharing and edit it into the
+// exact one).  R: this lane's run boundaries (bit i = point first + i).
+// Returns R plus every interior point of a run that lies strictly below the
+// chord of its run.  A vertex of the lower hull lies strictly below every
+// chord that spans it, so the result holds every hull vertex whatever the runs
+// are, and the Imminent Collisions rounds started from it remove the rest:
+// the runs only change the time, never the partition.  Prefix sums of every
+// point must be in s.X (the barrier here publishes them).  All threads call
+// this.
+__device__ __forceinline__ uint32_t candidate_boundaries(Smem& s, const Test& T, int t, int first, int n,
+                                                         uint32_t R) {
+    const int l = t & 31, w = t >> 5;
+    const int BIG = 1 << 20;
+    int lastS = R ? first + 31 - __clz((int)R) : -1, firstS = R ? first + __ffs((int)R) - 1 : BIG;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(WS_FULL_MASK, lastS, o), c = __shfl_down_sync(WS_FULL_MASK, firstS, o);
+        if (l >= o) lastS = max(lastS, a);
+        if (l + o < 32) firstS = min(firstS, c);
+    }
+    if (l == 31) s.wl[w] = lastS;
+    if (l == 0) s.wf[w] = firstS;
+    int pS = __shfl_up_sync(WS_FULL_MASK, lastS, 1), nS = __shfl_down_sync(WS_FULL_MASK, firstS, 1);
+    if (l == 0) pS = -1;
+    if (l == 31) nS = BIG;
+    __syncthreads();
+    for (int k = 0; k < w; ++k) pS = max(pS, s.wl[k]);
+    for (int k = w + 1; k < NW; ++k) nS = min(nS, s.wf[k]);
+    const int prevS = pS < 0 ? 0 : pS, nextS = nS >= BIG ? n : nS;
+    // interior points of this lane: 1 <= p <= n - 1 and not a run boundary
+    uint32_t bits = 0;
+    if (first < n) {
+        const int lo = first < 1 ? 1 : first, hi = min(first + M, n);   // points [lo, hi)
+        if (hi > lo) bits = (0xffffffffu >> (32 - (hi - lo))) << (lo - first);
+    }
+    bits &= ~R;
+    uint32_t F = 0;
+    while (bits) {
+        const int i = __ffs((int)bits) - 1;
+        bits &= bits - 1;
+        const int p = first + i;
+        const uint32_t below = R & ((1u << i) - 1u), above = R & ~((2u << i) - 1u);
+        const int a = below ? first + 31 - __clz((int)below) : prevS;
+        const int c = above ? first + __ffs((int)above) - 1 : nextS;
+        if (T(a, xat(s, a), p, xat(s, p), c, xat(s, c))) F |= 1u << i;
+    }
+    return R | F;
+}
+
 // The tile's hull by per-lane chains (stack form of pool-adjacent-violators),
 // the chord shortcut, a junction-local warp merge or the warp's tree of
 // bridge merges, and the CTA tree.  On return s.lo/s.hi/s.st hold the hull

@@ -120,7 +120,7 @@ template <typename T>
 cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
                             const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
                             const WsEpi& ep, uint32_t* status, cudaStream_t st, WsProf* prof, int32_t* gen_list,
-                            int32_t* gen_count, int ic_cap);
+                            int32_t* gen_count, int ic_cap, const int32_t* ids_prev);
 template <typename T>
 cudaError_t ws_launch_small_backward(const T* g, const int32_t* ids, const int64_t* offsets, const int32_t* seg_list,
                                      int n_list, T* gin, uint32_t* status, cudaStream_t st, WsProf* prof);

@@ -308,7 +308,8 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
                                                    const int32_t* __restrict__ seg_list,
                                                    const double* __restrict__ lambdas, T* out, int32_t* ids,
                                                    int64_t* n_clusters, int fp64, const WsEpi ep, uint32_t* status,
-                                                   int32_t* gen_list, int32_t* gen_count, int ic_cap) {
+                                                   int32_t* gen_list, int32_t* gen_count, int ic_cap,
+                                                   const int32_t* ids_prev) {   // (may alias ids)
     typedef KeyOf<T> KO;
     typedef typename KO::K K;
     typedef LeanSmem<T> S;
@@ -535,7 +536,40 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     __syncthreads();   // (the sort's scratch is dead: the hull's shared memory may be written)
     if (l == 31) h.wtot[w] = winc;
     if (t == 0) wsh::xref(h, 0) = 0;
+    // warm start: the earlier cluster ids by original position (low 16 bits;
+    // any values are valid), in the keys' storage (the keys are in registers)
+    uint16_t* cprev = reinterpret_cast<uint16_t*>(s.kv.keys);
+    if (ids_prev && first < n) {
+        const int32_t* src = ids_prev + a0 + first;
+        if (first + M <= n && (((uintptr_t)src) & 15) == 0) {
+#pragma unroll
+            for (int i = 0; i < M; i += 4) {
+                const int4 q = __ldcs(reinterpret_cast<const int4*>(src + i));
+                cprev[ipad(first + i)] = (uint16_t)q.x;
+                cprev[ipad(first + i + 1)] = (uint16_t)q.y;
+                cprev[ipad(first + i + 2)] = (uint16_t)q.z;
+                cprev[ipad(first + i + 3)] = (uint16_t)q.w;
+            }
+        } else {
+            for (int i = 0; i < M && first + i < n; ++i) cprev[ipad(first + i)] = (uint16_t)src[i];
+        }
+    }
     __syncthreads();
+    // ... and the runs of equal earlier ids along the sorted order: bit i = a
+    // run starts at point first + i
+    uint32_t Rrun = 0;
+    if (ids_prev && first < n) {
+        uint16_t cp = first >= 1 ? cprev[ipad(s.idx[ipad(first - 1)])] : (uint16_t)0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int p = first + i;
+            if (p < n) {
+                const uint16_t c = cprev[ipad(s.idx[ipad(p)])];
+                if (p >= 1 && c != cp) Rrun |= 1u << i;
+                cp = c;
+            }
+        }
+    }
     int64_t wbase = 0;
     for (int k = 0; k < w; ++k) wbase += h.wtot[k];
     const int64_t Xf = wbase + winc - csum;
@@ -551,9 +585,12 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     tst.P.modd = s.ts.modd;
     tst.P.sodd = s.ts.sodd;
     // round 1 of the Imminent Collisions rounds: boundaries where neighbours do
-    // not collide (the hull test on the consecutive points p-1, p, p+1)
+    // not collide (the hull test on the consecutive points p-1, p, p+1); or,
+    // warm, the candidate runs with the points below their chords
     uint32_t B = 0;
-    {
+    if (ids_prev) {
+        B = wsh::candidate_boundaries(h, tst, t, first, n, Rrun);
+    } else {
         int64_t dprev = devk(kprev);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
@@ -667,7 +704,7 @@ template <typename T>
 cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32_t* seg_list, int n_list,
                             const double* lambdas, T* out, int32_t* ids, int64_t* n_clusters, int fp64,
                             const WsEpi& ep, uint32_t* status, cudaStream_t st, WsProf* prof, int32_t* gen_list,
-                            int32_t* gen_count, int ic_cap) {
+                            int32_t* gen_count, int ic_cap, const int32_t* ids_prev) {
     constexpr int NT = 256;
     constexpr int M = SmallCfg<T>::M;
     if (n_list <= 0) return cudaSuccess;
@@ -678,7 +715,7 @@ cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32
     if (e != cudaSuccess) return e;
     WS_LAUNCH(prof, WSK_SMALL, st,
               (k_small<T><<<n_list, NT, smem, st>>>(values, offsets, seg_list, lambdas, out, ids, n_clusters, fp64, ep,
-                                                    status, gen_list, gen_count, ic_cap)));
+                                                    status, gen_list, gen_count, ic_cap, ids_prev)));
     // the segments the lean kernel passed on (none on ordinary inputs): a
     // small grid that walks the list
     const size_t gsmem = sizeof(SmallSmem<T, NT, M>);
@@ -693,7 +730,7 @@ cudaError_t ws_launch_small(const T* values, const int64_t* offsets, const int32
 
 template cudaError_t ws_launch_small<float>(const float*, const int64_t*, const int32_t*, int, const double*, float*,
                                             int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t, WsProf*,
-                                            int32_t*, int32_t*, int);
+                                            int32_t*, int32_t*, int, const int32_t*);
 template cudaError_t ws_launch_small<double>(const double*, const int64_t*, const int32_t*, int, const double*,
                                              double*, int32_t*, int64_t*, int, const WsEpi&, uint32_t*, cudaStream_t,
-                                             WsProf*, int32_t*, int32_t*, int);
+                                             WsProf*, int32_t*, int32_t*, int, const int32_t*);

@@ -17,9 +17,10 @@ from . import inputs, ws
 
 class ProxMLP:
     def __init__(self, sizes=inputs.MLP_SIZES, seed: int = 0, lr: float = 0.1, alpha: float = 1e-3,
-                 prec: str = "fp32comp", device="cuda"):
+                 prec: str = "fp32comp", device="cuda", warm: bool = False):
         self.sizes = tuple(sizes)
         self.lr, self.alpha, self.prec = lr, alpha, prec
+        self.warm = warm   # start every row's prox from the previous step's clusters (same result)
         mats = inputs.mlp_weights(seed, sizes)
         self.shapes = [m.shape for m in mats]
         numel = [m.size for m in mats]
@@ -32,7 +33,7 @@ class ProxMLP:
         self.plan = ws.Plan(self.offsets, torch.float32)
         n_rows = self.offsets.shape[0] - 1
         self.lams = torch.full((n_rows,), lr * alpha, dtype=torch.float64, device=device)
-        self.ids = torch.empty(self.flat.shape[0], dtype=torch.int32, device=device)
+        self.ids = torch.zeros(self.flat.shape[0], dtype=torch.int32, device=device)
         self.n_clusters = torch.zeros(n_rows, dtype=torch.int64, device=device)
         self.biases = [torch.zeros(r, device=device) for r, _ in self.shapes]
 
@@ -61,7 +62,7 @@ class ProxMLP:
     def prox(self, stream=None):
         """prox_{lr alpha R} of every row, from self.flat into self.flat_out; then swap."""
         self.plan.forward(self.flat, self.lams, self.prec, out=self.flat_out, id_out=self.ids,
-                          n_clusters=self.n_clusters, stream=stream)
+                          n_clusters=self.n_clusters, stream=stream, ids_prev=self.ids if self.warm else None)
         self.flat, self.flat_out = self.flat_out, self.flat
 
     def step(self, x, y):

@@ -54,6 +54,7 @@ def _load():
             lib.ws_plan_destroy.argtypes = [_vp]
             lib.ws_plan_destroy.restype = None
             lib.ws_prox_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+            lib.ws_prox_batched_warm.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
             lib.ws_prox.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]
             lib.ws_R.argtypes = [_vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
             lib.ws_prox_dlambda_batched.argtypes = [_vp, _vp, _vp, _vp, _vp]
@@ -335,7 +336,9 @@ class Plan:
         return self
 
     def forward(self, values: torch.Tensor, lambdas: torch.Tensor, prec: str = "fp32comp", ids: bool = True,
-                out=None, id_out=None, n_clusters=None, stream=None):
+                out=None, id_out=None, n_clusters=None, stream=None, ids_prev=None):
+        """ws_prox_batched; with ids_prev (int32, one per element, e.g. the previous
+        step's cluster ids, may be id_out itself) ws_prox_batched_warm: same outputs."""
         if values.dtype != self.dtype or values.shape[0] != self.n or not values.is_cuda:
             raise ValueError("values must be a CUDA tensor of the plan's dtype and length")
         if lambdas.dtype != torch.float64 or lambdas.shape[0] != self.n_seg or not lambdas.is_cuda:
@@ -345,8 +348,16 @@ class Plan:
             else id_out
         nc = torch.zeros(max(self.n_seg, 1), dtype=torch.int64, device=values.device) if n_clusters is None \
             else n_clusters
-        _check(_load().ws_prox_batched(self.handle, _ptr(values), _ptr(lambdas), _ptr(out), _ptr(idt), _ptr(nc),
-                                       PREC[prec], _stream(stream)), "ws_prox_batched")
+        if ids_prev is None:
+            _check(_load().ws_prox_batched(self.handle, _ptr(values), _ptr(lambdas), _ptr(out), _ptr(idt), _ptr(nc),
+                                           PREC[prec], _stream(stream)), "ws_prox_batched")
+        else:
+            if (ids_prev.dtype != torch.int32 or ids_prev.dim() != 1 or ids_prev.shape[0] != self.n
+                    or not ids_prev.is_cuda or not ids_prev.is_contiguous()):
+                raise ValueError("ids_prev must be a contiguous 1-D int32 CUDA tensor of the plan's length")
+            _check(_load().ws_prox_batched_warm(self.handle, _ptr(values), _ptr(lambdas), _ptr(ids_prev), _ptr(out),
+                                                _ptr(idt), _ptr(nc), PREC[prec], _stream(stream)),
+                   "ws_prox_batched_warm")
         return out, idt, nc
 
     def forward_l1(self, values: torch.Tensor, lambdas: torch.Tensor, beta: float, rho: float = 0.0,
