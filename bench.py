@@ -55,12 +55,10 @@ ONE_CTA_MAX_F32 = 4096   # FP32 segments up to this length run one CTA each
 MODEL_B = {"key_only_52B": 52, "index_payload_80B": 80}
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture, and the hash of the kernel sources it was taken on; reported as
-# null once the sources change.  tile_hull: captured at d = 2^24 (lambda = 1),
-# 170.7 MB per launch, scaled by the element count to d = 2^26 (the kernel's
-# traffic grows with the elements it processes); see profiles/.
-NCU_TRAFFIC = {"tile_hull": 170.657e6 * 4}
-NCU_SOURCE_HASH = "8e50713d8ea45151"
+# ncu capture of the bench's own workload, and the hash of the kernel sources it
+# was taken on; reported as null once the sources change (see profiles/).
+NCU_TRAFFIC = {}
+NCU_SOURCE_HASH = ""
 
 
 def source_hash() -> str:
@@ -418,6 +416,31 @@ def bench_train(ws, ctx, stream, steps=10):
     return res
 
 
+def run_rows_case(args):
+    """The batched MLP rows (8202 segments of 3072/4096, one-CTA kernel) alone:
+    warm-up + steps forward calls, CUDA-event time of the steps."""
+    import torch
+
+    import __graft_entry__
+    from paper_2311_03096_gb300 import inputs, ws
+
+    __graft_entry__.build()
+    ctx = ws.Context.get(0)
+    stream = torch.cuda.current_stream()
+    vals, off, lam, kinds = inputs.batched_segments(seed=args.seed, layers=False, extra=0)
+    plan = ws.Plan(off, torch.float32, ctx=ctx)
+    v = torch.from_numpy(vals).cuda()
+    lt = torch.from_numpy(lam).cuda()
+    out = torch.empty_like(v)
+    ids = torch.empty(v.shape[0], dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        plan.forward(v, lt, args.prec, out=out, id_out=ids, stream=stream)
+    ms = _time_calls(lambda: plan.forward(v, lt, args.prec, out=out, id_out=ids, stream=stream), stream,
+                     max(args.steps, 1))
+    ctx.check(what="rows case")
+    print(json.dumps({"case": "rows", "segments": int(len(lam)), "elements": int(off[-1]), "ms_per_call": ms}))
+
+
 def config_dict(args, world):
     return {"workload": WORKLOAD, "d": args.d, "lambdas": list(LAMBDAS), "storage": "f32", "prec": args.prec,
             "arithmetic": "merge decisions exact in 64/128-bit fixed point; cluster values in "
@@ -438,11 +461,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--case", default="single", choices=["single", "rows"],
+                    help="rows: only run the batched MLP rows forward (warm-up + steps calls) and print its "
+                         "ms per call -- the launch that the one-CTA kernel's profiles capture")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.case == "rows":
+        run_rows_case(args)
         return
 
     import torch
