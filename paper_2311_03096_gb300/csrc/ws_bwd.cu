@@ -15,7 +15,7 @@
 // cluster slots cleared (k_bwd_zero), the sums (k_bwd_accum: lanes of a warp
 // with the same cluster add once, and a tile whose elements all share one
 // cluster adds once per CTA, so a single huge cluster costs one atomic per
-// 8192 elements), the means (k_bwd_mean), the gather (k_bwd_apply).
+// sort tile), the means (k_bwd_mean), the gather (k_bwd_apply).
 // One-CTA segments: the same arithmetic in shared memory (k_small_backward).
 #include "ws_kernels.cuh"
 

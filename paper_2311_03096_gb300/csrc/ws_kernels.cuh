@@ -36,9 +36,9 @@ struct WsProf {
 
 // Large-path tile geometry.
 constexpr int WS_SORT_NT = 512;              // threads per onesweep CTA
-constexpr int WS_SORT_ITEMS = 16;            // keys per thread
+constexpr int WS_SORT_ITEMS = 12;            // keys per thread (a multiple of 4: 16-byte loads in k_hist)
 constexpr int WS_SORT_CHAINS = 1;            // independent ranking chains per warp
-constexpr int WS_SORT_TILE = WS_SORT_NT * WS_SORT_ITEMS;   // 8192 keys per sort tile
+constexpr int WS_SORT_TILE = WS_SORT_NT * WS_SORT_ITEMS;   // 6144 keys per sort tile
 constexpr int WS_HULL_NT = 256;              // threads per hull-tile CTA
 constexpr int WS_HULL_M = 16;                // points per thread chunk
 constexpr int WS_HULL_TILE = WS_HULL_NT * WS_HULL_M;       // 4096 elements per hull tile

@@ -8,7 +8,7 @@
 //
 // One histogram pass computes every digit histogram of every large segment;
 // then each 8-bit digit pass is a single "onesweep" kernel: a CTA ranks its
-// 8192 keys by digit in shared memory, publishes its per-digit counts, gets
+// 6144 keys by digit in shared memory, publishes its per-digit counts, gets
 // the counts of the earlier tiles of the same segment through a decoupled
 // look-back (bounded waits), and writes its keys as per-digit contiguous runs.
 #include "ws_kernels.cuh"
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_hist_scan(uint32_t* hist, uint32_t* epo
 }
 
 template <typename T, bool FIRST>
-__global__ void __launch_bounds__(WS_SORT_NT, 2) k_onesweep(const T* __restrict__ values,
+__global__ void __launch_bounds__(WS_SORT_NT, sizeof(T) == 4 ? 3 : 2) k_onesweep(const T* __restrict__ values,
                                                             const typename KeyOf<T>::K* __restrict__ keys_in,
                                                             typename KeyOf<T>::K* __restrict__ keys_out,
                                                             const TileDesc* __restrict__ tiles,
