@@ -92,6 +92,10 @@ struct ws_plan {
     int32_t* bcnt = nullptr;
     unsigned long long* bacc = nullptr;
     int32_t* bwd_seg = nullptr;
+    // plans with both one-CTA and device-wide segments: the one-CTA kernel
+    // runs on this stream, forked from and joined back into the caller's
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -215,6 +219,14 @@ ws_status build_plan(ws_plan* p) {
     }
     p->n_small = (int)small.size();
     p->n_lseg = (int)lsegs.size();
+    if (p->n_small > 0 && p->n_lseg > 0) {
+        if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return WS_ERR_CUDA;
+        }
+    }
     p->n_sort_tiles = (int)stiles.size();
     p->n_hull_tiles = (int)htiles.size();
     p->n_keys = kpos;
@@ -284,35 +296,65 @@ ws_status map_cuda(cudaError_t e) {
     return e == cudaErrorMemoryAllocation ? WS_ERR_NOMEM : WS_ERR_CUDA;
 }
 
+// The one-CTA segments and the device-wide chain touch disjoint elements, so
+// with both present the one-CTA kernel runs on the plan's side stream, after
+// everything already queued on the caller's stream (fork) and before anything
+// queued there after this call (join).  Event record/wait pairs: capturable.
+// *ss: the stream for the one-CTA kernel (st itself without a side stream);
+// false on a CUDA error.
+bool fork(ws_plan* p, cudaStream_t st, cudaStream_t* ss) {
+    *ss = st;
+    if (!p->side) return true;
+    if (cudaEventRecord(p->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(p->side, p->ev_fork, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *ss = p->side;
+    return true;
+}
+
+bool join(ws_plan* p, cudaStream_t st) {
+    if (!p->side) return true;
+    if (cudaEventRecord(p->ev_join, p->side) != cudaSuccess || cudaStreamWaitEvent(st, p->ev_join, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 template <typename T>
 ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, void* out, int32_t* ids,
                       int64_t* n_clusters, ws_prec prec, const WsEpi& ep, cudaStream_t st,
                       const int32_t* ids_prev = nullptr) {
     const int fp64 = prec == WS_PREC_FP64 ? 1 : 0;
+    cudaStream_t ss;
+    if (!fork(p, st, &ss)) return WS_ERR_CUDA;
     cudaError_t e = ws_launch_small<T>((const T*)values, p->d_offsets, p->d_small, p->n_small, lambdas, (T*)out, ids,
-                                       n_clusters, fp64, ep, p->ctx->status, st, &p->ctx->prof, p->small_gen,
+                                       n_clusters, fp64, ep, p->ctx->status, ss, &p->ctx->prof, p->small_gen,
                                        p->small_gen_count, p->ctx->ic_cap, ids_prev);
-    if (e) return map_cuda(e);
+    if (e) { join(p, st); return map_cuda(e); }
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);
         e = ws_large_prox<T>(W, (const T*)values, lambdas, (T*)out, ids, n_clusters, fp64, ep, p->ctx->status,
                              p->ctx->spin_limit, p->n_levels, st);
-        if (e) return map_cuda(e);
     }
-    return WS_OK;
+    if (!join(p, st)) return WS_ERR_CUDA;
+    return e ? map_cuda(e) : WS_OK;
 }
 
 template <typename T>
 ws_status run_backward(ws_plan* p, const void* g, const int32_t* ids, void* gin, cudaStream_t st) {
+    cudaStream_t ss;
+    if (!fork(p, st, &ss)) return WS_ERR_CUDA;
     cudaError_t e = ws_launch_small_backward<T>((const T*)g, ids, p->d_offsets, p->d_small, p->n_small, (T*)gin,
-                                                p->ctx->status, st, &p->ctx->prof);
-    if (e) return map_cuda(e);
+                                                p->ctx->status, ss, &p->ctx->prof);
+    if (e) { join(p, st); return map_cuda(e); }
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);
         e = ws_large_backward<T>(W, (const T*)g, ids, (T*)gin, p->ctx->status, st);
-        if (e) return map_cuda(e);
     }
-    return WS_OK;
+    if (!join(p, st)) return WS_ERR_CUDA;
+    return e ? map_cuda(e) : WS_OK;
 }
 
 ws_status plan_create_impl(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, int64_t n_seg, ws_dtype dtype,
@@ -415,6 +457,9 @@ ws_status ws_plan_create(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, in
 
 void ws_plan_destroy(ws_plan* plan) {
     if (!plan) return;
+    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    if (plan->side) cudaStreamDestroy(plan->side);
     for (void* a : plan->allocs) cudaFree(a);
     delete plan;
 }

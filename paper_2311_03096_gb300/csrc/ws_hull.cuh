@@ -89,8 +89,13 @@ struct Smem {
     int wsum[NW];
     int general;                 // a bridge walk hit its cap: the tile needs the general kernel
     int all_conc;
-    int wl[NW], wlr[NW], wf[NW], wfr[NW];   // IC rounds, per warp: last survivor / removal, first ones
+    // IC rounds, per warp: last survivor / removal, first ones (read as int4)
+    __align__(16) int wl[NW];
+    __align__(16) int wlr[NW];
+    __align__(16) int wf[NW];
+    __align__(16) int wfr[NW];
 };
+static_assert(NW % 4 == 0, "per-warp words are read four at a time");
 
 __device__ __forceinline__ int own_warp(int p) { return p ? (p - 1) / WP : 0; }
 __device__ __forceinline__ int64_t& xref(Smem& s, int p) {
@@ -546,6 +551,64 @@ __device__ __forceinline__ void cta_tree(Smem& s, const Test& T, int t, int cap)
 // When a round removes nothing, every adjacent pair of blocks has increasing
 // means: the blocks are the tile's pool-adjacent-violators partition and
 // their boundaries (with points 0 and n) the vertices of its lower hull.
+// For this lane's range of points: the last set point before it and the first
+// one after it, over the whole CTA, for two point sets at once (B: current
+// boundaries, R: last round's removals; bit i = point first + i).  Inside the
+// warp by ballots and one shuffle each, across warps through one word per
+// warp and set (one barrier).  -1 / BIG when there is none.
+struct Around { int pS, nS, pR, nR; };
+__device__ __forceinline__ Around around(Smem& s, int t, int first, uint32_t B, uint32_t R) {
+    const int l = t & 31, w = t >> 5;
+    const int BIG = 1 << 20;
+    const int myLS = B ? first + 31 - __clz((int)B) : -1, myFS = B ? first + __ffs((int)B) - 1 : BIG;
+    const int myLR = R ? first + 31 - __clz((int)R) : -1, myFR = R ? first + __ffs((int)R) - 1 : BIG;
+    const unsigned bS = __ballot_sync(WS_FULL_MASK, B != 0), bR = __ballot_sync(WS_FULL_MASK, R != 0);
+    const unsigned lt = (1u << l) - 1u, gt = l == 31 ? 0u : ~((2u << l) - 1u);
+    auto below = [&](unsigned m, int v) {   // v of the highest lane of m below this one
+        const unsigned mm = m & lt;
+        const int x = __shfl_sync(WS_FULL_MASK, v, mm ? 31 - __clz((int)mm) : l);
+        return mm ? x : -1;
+    };
+    auto above = [&](unsigned m, int v) {   // v of the lowest lane of m above this one
+        const unsigned mm = m & gt;
+        const int x = __shfl_sync(WS_FULL_MASK, v, mm ? __ffs((int)mm) - 1 : l);
+        return mm ? x : BIG;
+    };
+    Around r;
+    r.pS = below(bS, myLS);
+    r.pR = below(bR, myLR);
+    r.nS = above(bS, myFS);
+    r.nR = above(bR, myFR);
+    // the warp's own last / first points of each set
+    const int wLS = __shfl_sync(WS_FULL_MASK, myLS, bS ? 31 - __clz((int)bS) : 0);
+    const int wLR = __shfl_sync(WS_FULL_MASK, myLR, bR ? 31 - __clz((int)bR) : 0);
+    const int wFS = __shfl_sync(WS_FULL_MASK, myFS, bS ? __ffs((int)bS) - 1 : 0);
+    const int wFR = __shfl_sync(WS_FULL_MASK, myFR, bR ? __ffs((int)bR) - 1 : 0);
+    if (l == 0) {
+        s.wl[w] = bS ? wLS : -1;
+        s.wlr[w] = bR ? wLR : -1;
+        s.wf[w] = bS ? wFS : BIG;
+        s.wfr[w] = bR ? wFR : BIG;
+    }
+    __syncthreads();
+    int wl[NW], wlr[NW], wf[NW], wfr[NW];
+#pragma unroll
+    for (int j = 0; j < NW / 4; ++j) {
+        const int4 a = reinterpret_cast<const int4*>(s.wl)[j], b = reinterpret_cast<const int4*>(s.wlr)[j];
+        const int4 c = reinterpret_cast<const int4*>(s.wf)[j], d = reinterpret_cast<const int4*>(s.wfr)[j];
+        wl[4 * j] = a.x; wl[4 * j + 1] = a.y; wl[4 * j + 2] = a.z; wl[4 * j + 3] = a.w;
+        wlr[4 * j] = b.x; wlr[4 * j + 1] = b.y; wlr[4 * j + 2] = b.z; wlr[4 * j + 3] = b.w;
+        wf[4 * j] = c.x; wf[4 * j + 1] = c.y; wf[4 * j + 2] = c.z; wf[4 * j + 3] = c.w;
+        wfr[4 * j] = d.x; wfr[4 * j + 1] = d.y; wfr[4 * j + 2] = d.z; wfr[4 * j + 3] = d.w;
+    }
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        if (k < w) { r.pS = max(r.pS, wl[k]); r.pR = max(r.pR, wlr[k]); }
+        if (k > w) { r.nS = min(r.nS, wf[k]); r.nR = min(r.nR, wfr[k]); }
+    }
+    return r;
+}
+
 // B: this lane's round-1 boundaries (bit i = point first + i); on return the
 // surviving ones.  Returns true if the rounds converged within `cap` rounds
 // (rounds = rounds run, the final unchanged one included).  Prefix sums of
@@ -553,7 +616,6 @@ __device__ __forceinline__ void cta_tree(Smem& s, const Test& T, int t, int cap)
 // threads of the CTA call this.
 __device__ __forceinline__ bool ic_rounds(Smem& s, const Test& T, int t, int first, int n, uint32_t& B, int cap,
                                           int& rounds) {
-    const int l = t & 31, w = t >> 5;
     rounds = 1;
     if (!__syncthreads_or(B != 0)) { rounds = 2; return true; }   // one block: the chord (round 2 has nothing to do)
     uint32_t D = B, Rprev = 0;
@@ -562,27 +624,8 @@ __device__ __forceinline__ bool ic_rounds(Smem& s, const Test& T, int t, int fir
         ++rounds;
         // neighbouring boundaries outside this lane's range, and where last
         // round's removals were
-        int lastS = B ? first + 31 - __clz((int)B) : -1, firstS = B ? first + __ffs((int)B) - 1 : BIG;
-        int lastR = Rprev ? first + 31 - __clz((int)Rprev) : -1;
-        int firstR = Rprev ? first + __ffs((int)Rprev) - 1 : BIG;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int a = __shfl_up_sync(WS_FULL_MASK, lastS, o), b = __shfl_up_sync(WS_FULL_MASK, lastR, o);
-            const int c = __shfl_down_sync(WS_FULL_MASK, firstS, o);
-            const int e = __shfl_down_sync(WS_FULL_MASK, firstR, o);
-            if (l >= o) { lastS = max(lastS, a); lastR = max(lastR, b); }
-            if (l + o < 32) { firstS = min(firstS, c); firstR = min(firstR, e); }
-        }
-        // (inclusive scans: lane 31 / lane 0 hold the warp's totals)
-        if (l == 31) { s.wl[w] = lastS; s.wlr[w] = lastR; }
-        if (l == 0) { s.wf[w] = firstS; s.wfr[w] = firstR; }
-        int pS = __shfl_up_sync(WS_FULL_MASK, lastS, 1), pR = __shfl_up_sync(WS_FULL_MASK, lastR, 1);
-        int nS = __shfl_down_sync(WS_FULL_MASK, firstS, 1), nR = __shfl_down_sync(WS_FULL_MASK, firstR, 1);
-        if (l == 0) { pS = -1; pR = -1; }
-        if (l == 31) { nS = BIG; nR = BIG; }
-        __syncthreads();
-        for (int k = 0; k < w; ++k) { pS = max(pS, s.wl[k]); pR = max(pR, s.wlr[k]); }
-        for (int k = w + 1; k < NW; ++k) { nS = min(nS, s.wf[k]); nR = min(nR, s.wfr[k]); }
+        const Around ar = around(s, t, first, B, Rprev);
+        const int pS = ar.pS, nS = ar.nS, pR = ar.pR, nR = ar.nR;
         const int prevS = pS < 0 ? 0 : pS, nextS = nS >= BIG ? n : nS;
         // the end survivors' outer neighbours changed if a removal lay between
         if (B) {
@@ -634,23 +677,9 @@ __device__ __forceinline__ bool ic_rounds(Smem& s, const Test& T, int t, int fir
 // this.
 __device__ __forceinline__ uint32_t candidate_boundaries(Smem& s, const Test& T, int t, int first, int n,
                                                          uint32_t R) {
-    const int l = t & 31, w = t >> 5;
     const int BIG = 1 << 20;
-    int lastS = R ? first + 31 - __clz((int)R) : -1, firstS = R ? first + __ffs((int)R) - 1 : BIG;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int a = __shfl_up_sync(WS_FULL_MASK, lastS, o), c = __shfl_down_sync(WS_FULL_MASK, firstS, o);
-        if (l >= o) lastS = max(lastS, a);
-        if (l + o < 32) firstS = min(firstS, c);
-    }
-    if (l == 31) s.wl[w] = lastS;
-    if (l == 0) s.wf[w] = firstS;
-    int pS = __shfl_up_sync(WS_FULL_MASK, lastS, 1), nS = __shfl_down_sync(WS_FULL_MASK, firstS, 1);
-    if (l == 0) pS = -1;
-    if (l == 31) nS = BIG;
-    __syncthreads();
-    for (int k = 0; k < w; ++k) pS = max(pS, s.wl[k]);
-    for (int k = w + 1; k < NW; ++k) nS = min(nS, s.wf[k]);
+    const Around ar = around(s, t, first, R, 0u);
+    const int pS = ar.pS, nS = ar.nS;
     const int prevS = pS < 0 ? 0 : pS, nextS = nS >= BIG ? n : nS;
     // interior points of this lane: 1 <= p <= n - 1 and not a run boundary
     uint32_t bits = 0;
