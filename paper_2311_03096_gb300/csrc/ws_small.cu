@@ -288,7 +288,7 @@ struct LeanSmem {
             uint32_t dcount[256], dstart[256];
         } sort;
         struct {
-            int cnt[CAP];       // bucket counts, then starts
+            int cnt[CAP + CAP / 16];   // bucket counts, then starts (padded like the keys: kpad)
         } bucket;
         wsh::Smem h;
         uint16_t cid_of[CAP + CAP / 8];   // cluster of every original position (after the values)
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
             hi = max(hi, ws_shfl_xor_k(hi, o));
         }
         int* cnt = s.u.bucket.cnt;
-        for (int i = t; i < n; i += NT) cnt[i] = 0;
+        for (int i = t; i < n; i += NT) cnt[kpad(i)] = 0;
         __syncthreads();
         if (l == 0) { ws_atomic_min_k(&s.kmin, lo); ws_atomic_max_k(&s.kmax, hi); }
     }
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
             if (first + i < n) {
                 const float f = ((float)KO::from_key(key[i]) - f0) * scale;
                 bk[i] = min(n - 1, max(0, (int)f));
-                rk[i] = atomicAdd(&cnt[bk[i]], 1);
+                rk[i] = atomicAdd(&cnt[kpad(bk[i])], 1);
             }
         }
         __syncthreads();
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
         int c[M], sum = 0, big = 0;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            c[i] = (first + i < n) ? cnt[first + i] : 0;
+            c[i] = (first + i < n) ? cnt[kpad(first + i)] : 0;
             sum += c[i];
             big = max(big, c[i]);
         }
@@ -433,22 +433,51 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
         int run = ws_block_excl_scan<NT, int>(sum, s.wsumi, &tot);
 #pragma unroll
         for (int i = 0; i < M; ++i)
-            if (first + i < n) { cnt[first + i] = run; run += c[i]; }
+            if (first + i < n) { cnt[kpad(first + i)] = run; run += c[i]; }
         radix = __syncthreads_or(big > BUCKET_MAX);
         if (!radix) {
 #pragma unroll
             for (int i = 0; i < M; ++i)
                 if (first + i < n) {
-                    const int pp = cnt[bk[i]] + rk[i];
+                    const int pp = cnt[kpad(bk[i])] + rk[i];
                     s.kv.keys[kpad(pp)] = key[i];
                     s.idx[ipad(pp)] = (uint16_t)(first + i);
                 }
             __syncthreads();
-            // each bucket by key (insertion sort; ties may end in any order)
-#pragma unroll 1
-            for (int i = 0; i < M; ++i) {
-                if (first + i >= n || c[i] < 2) continue;
-                const int b0 = cnt[first + i], b1 = b0 + c[i];
+            // each bucket by key (ties may end in any order): up to four
+            // elements by a sorting network in registers, larger buckets by
+            // insertion in shared memory.  Bucket ends from the starts (no
+            // indexing of c[] by a loop variable: it would live in local memory).
+            uint32_t multi = 0;
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+                if (first + i < n && c[i] >= 2) multi |= 1u << i;
+            while (multi) {
+                const int i = __ffs((int)multi) - 1;
+                multi &= multi - 1;
+                const int b0 = cnt[kpad(first + i)];
+                const int b1 = first + i + 1 < n ? cnt[kpad(first + i + 1)] : n;
+                if (b1 - b0 <= 4) {
+                    K k[4];
+                    uint16_t x[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool in = b0 + j < b1;
+                        k[j] = in ? s.kv.keys[kpad(b0 + j)] : ~(K)0;
+                        x[j] = in ? s.idx[ipad(b0 + j)] : (uint16_t)0;
+                    }
+                    auto cs = [&](int a, int b) {
+                        const bool sw = k[a] > k[b];
+                        const K ka = sw ? k[b] : k[a], kb = sw ? k[a] : k[b];
+                        const uint16_t xa = sw ? x[b] : x[a], xb = sw ? x[a] : x[b];
+                        k[a] = ka; k[b] = kb; x[a] = xa; x[b] = xb;
+                    };
+                    cs(0, 1); cs(2, 3); cs(0, 2); cs(1, 3); cs(1, 2);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (b0 + j < b1) { s.kv.keys[kpad(b0 + j)] = k[j]; s.idx[ipad(b0 + j)] = x[j]; }
+                    continue;
+                }
                 for (int a = b0 + 1; a < b1; ++a) {
                     const K kk = s.kv.keys[kpad(a)];
                     const uint16_t ii = s.idx[ipad(a)];
@@ -642,17 +671,20 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
                 }
             }
             const int64_t xd = wsh::xat(h, b) - wsh::xat(h, a);
+            K ki = kr[0];   // kr[i] by selects (a loop-variable index would put kr in local memory)
+#pragma unroll
+            for (int j = 1; j < M; ++j) ki = (i == j) ? kr[j] : ki;
             if (KO::BITS == 32 && !fp64) {
                 // FP32: mean = x_0 + (deviation sum / count) in tile units; every
                 // term exact but the conversions (a few FP32 ulps of max |w|)
-                const float xa = (float)KO::from_key(kr[i]);
+                const float xa = (float)KO::from_key(ki);
                 const float mean = (b - a == 1) ? xa
                                                 : x0f + ldexpf(ws_u64_to_float((uint64_t)xd) / (float)(b - a), -s.ts.sc.L);
                 s.kv.vals[r] = (T)ws_epilogue<float>(mean, s.sc.mu_f * (float)(n - a - b), ep.beta_f, ep.gamma_f,
                                                      ep.on != 0);
             } else {
                 const i128 SX = (i128)(b - a) * (i128)q0 + (bin ? ((i128)xd << sh) : (i128)xd);
-                s.kv.vals[r] = ValueOut<T>::value(SX, a, b, KO::from_key(kr[i]), s.sc, fp64 != 0, ep);
+                s.kv.vals[r] = ValueOut<T>::value(SX, a, b, KO::from_key(ki), s.sc, fp64 != 0, ep);
             }
             ++r;
         }
