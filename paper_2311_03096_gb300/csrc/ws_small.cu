@@ -302,6 +302,96 @@ struct LeanSmem {
     int flags, emin;
 };
 
+__device__ __forceinline__ int lean_kpad(int p) { return p + (p >> 4); }          // keys, counts
+__device__ __forceinline__ int lean_ipad(int p) { return p + ((p >> 4) << 1); }   // 16-bit arrays
+
+// The rare paths of k_small live out of line so that the common path's code
+// stays compact in the instruction cache.  All threads of the CTA call each.
+
+// LSD radix sort, 8-bit digits, of the n (key, original position) pairs in
+// s.kv.keys / s.idx (any order on entry; sorted on return).  Every pass takes
+// position w*32*M + k*32 + l of the previous one, which the stable ranking
+// keeps in order.
+template <typename T>
+__device__ __noinline__ void small_radix(LeanSmem<T>& s, int n) {
+    typedef KeyOf<T> KO;
+    typedef typename KO::K K;
+    constexpr int NT = wsh::NT, M = wsh::M;
+    const int t = threadIdx.x, l = t & 31, w = t >> 5;
+    for (int pass = 0; pass < KO::BITS / 8; ++pass) {
+        K key[M];
+        uint16_t ii[M];
+        uint32_t dg[M];
+        bool valid[M];
+        int pos[M];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int p = w * 32 * M + k * 32 + l;
+            valid[k] = p < n;
+            key[k] = valid[k] ? s.kv.keys[lean_kpad(p)] : (K)0;
+            ii[k] = valid[k] ? s.idx[lean_ipad(p)] : (uint16_t)0;
+            dg[k] = (uint32_t)((key[k] >> (8 * pass)) & 0xff);
+        }
+        __syncthreads();
+        ws_rank_digits<NT, M, 1>(dg, valid, pos, s.u.sort.whist, s.u.sort.dcount, s.u.sort.dstart);
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+            if (valid[k]) { s.kv.keys[lean_kpad(pos[k])] = key[k]; s.idx[lean_ipad(pos[k])] = ii[k]; }
+        __syncthreads();
+    }
+}
+
+// The hull by chains and trees when the rounds hit their cap (no CTA cap:
+// never fails).  Ends synchronised.
+__device__ __noinline__ void small_chain_tree(wsh::Smem& h, const wsh::Test& tst, int first, int last, int n,
+                                              int64_t Xf) {
+    wsh::chain_tree_hull(h, tst, threadIdx.x, first, last, n, Xf, 1 << 30);
+}
+
+// Warm start: the runs of equal earlier cluster ids (low 16 bits; any values
+// are valid) along the sorted order, then candidate_boundaries.  The earlier
+// ids are staged by original position in `cprev` (the keys' storage: the
+// keys are in registers by now).  Prefix sums of every point must be written
+// (the barriers here publish them).
+template <typename T>
+__device__ __noinline__ uint32_t small_warm(LeanSmem<T>& s, const wsh::Test& tst, const int32_t* ids_prev,
+                                            int64_t a0, int first, int n) {
+    constexpr int M = wsh::M;
+    const int t = threadIdx.x;
+    uint16_t* cprev = reinterpret_cast<uint16_t*>(s.kv.keys);
+    if (first < n) {
+        const int32_t* src = ids_prev + a0 + first;
+        if (first + M <= n && (((uintptr_t)src) & 15) == 0) {
+#pragma unroll
+            for (int i = 0; i < M; i += 4) {
+                const int4 q = __ldcs(reinterpret_cast<const int4*>(src + i));
+                cprev[lean_ipad(first + i)] = (uint16_t)q.x;
+                cprev[lean_ipad(first + i + 1)] = (uint16_t)q.y;
+                cprev[lean_ipad(first + i + 2)] = (uint16_t)q.z;
+                cprev[lean_ipad(first + i + 3)] = (uint16_t)q.w;
+            }
+        } else {
+            for (int i = 0; i < M && first + i < n; ++i) cprev[lean_ipad(first + i)] = (uint16_t)src[i];
+        }
+    }
+    __syncthreads();
+    // bit i: a run starts at point first + i
+    uint32_t R = 0;
+    if (first < n) {
+        uint16_t cp = first >= 1 ? cprev[lean_ipad(s.idx[lean_ipad(first - 1)])] : (uint16_t)0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const int p = first + i;
+            if (p < n) {
+                const uint16_t c = cprev[lean_ipad(s.idx[lean_ipad(p)])];
+                if (p >= 1 && c != cp) R |= 1u << i;
+                cp = c;
+            }
+        }
+    }
+    return wsh::candidate_boundaries(s.u.h, tst, t, first, n, R);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const T* __restrict__ values,
                                                    const int64_t* __restrict__ offsets,
@@ -494,34 +584,13 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
             __syncthreads();
         }
     }
-    // ---- otherwise: LSD radix sort, 8-bit digits.  The first pass ranks the
-    // loaded elements directly (any order is fine before the first pass);
-    // later passes take position w*32*M + k*32 + l of the previous one, which
-    // the stable ranking keeps in order.
-    for (int pass = 0; radix && pass < KO::BITS / 8; ++pass) {
-        uint16_t ii[M];
-        uint32_t dg[M];
-        bool valid[M];
-        int pos[M];
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-            if (pass == 0) {
-                valid[k] = first + k < n;
-                ii[k] = (uint16_t)(first + k);
-            } else {
-                const int p = w * 32 * M + k * 32 + l;
-                valid[k] = p < n;
-                key[k] = valid[k] ? s.kv.keys[kpad(p)] : (K)0;
-                ii[k] = valid[k] ? s.idx[ipad(p)] : (uint16_t)0;
-            }
-            dg[k] = (uint32_t)((key[k] >> (8 * pass)) & 0xff);
-        }
-        __syncthreads();
-        ws_rank_digits<NT, M, 1>(dg, valid, pos, s.u.sort.whist, s.u.sort.dcount, s.u.sort.dstart);
+    // ---- otherwise: LSD radix sort, 8-bit digits (out of line)
+    if (radix) {
 #pragma unroll
         for (int k = 0; k < M; ++k)
-            if (valid[k]) { s.kv.keys[kpad(pos[k])] = key[k]; s.idx[ipad(pos[k])] = ii[k]; }
+            if (first + k < n) { s.kv.keys[kpad(first + k)] = key[k]; s.idx[ipad(first + k)] = (uint16_t)(first + k); }
         __syncthreads();
+        small_radix<T>(s, n);
     }
 
     // ---- the sorted segment as one hull tile: this thread's 16 sorted keys
@@ -565,40 +634,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     __syncthreads();   // (the sort's scratch is dead: the hull's shared memory may be written)
     if (l == 31) h.wtot[w] = winc;
     if (t == 0) wsh::xref(h, 0) = 0;
-    // warm start: the earlier cluster ids by original position (low 16 bits;
-    // any values are valid), in the keys' storage (the keys are in registers)
-    uint16_t* cprev = reinterpret_cast<uint16_t*>(s.kv.keys);
-    if (ids_prev && first < n) {
-        const int32_t* src = ids_prev + a0 + first;
-        if (first + M <= n && (((uintptr_t)src) & 15) == 0) {
-#pragma unroll
-            for (int i = 0; i < M; i += 4) {
-                const int4 q = __ldcs(reinterpret_cast<const int4*>(src + i));
-                cprev[ipad(first + i)] = (uint16_t)q.x;
-                cprev[ipad(first + i + 1)] = (uint16_t)q.y;
-                cprev[ipad(first + i + 2)] = (uint16_t)q.z;
-                cprev[ipad(first + i + 3)] = (uint16_t)q.w;
-            }
-        } else {
-            for (int i = 0; i < M && first + i < n; ++i) cprev[ipad(first + i)] = (uint16_t)src[i];
-        }
-    }
     __syncthreads();
-    // ... and the runs of equal earlier ids along the sorted order: bit i = a
-    // run starts at point first + i
-    uint32_t Rrun = 0;
-    if (ids_prev && first < n) {
-        uint16_t cp = first >= 1 ? cprev[ipad(s.idx[ipad(first - 1)])] : (uint16_t)0;
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-            const int p = first + i;
-            if (p < n) {
-                const uint16_t c = cprev[ipad(s.idx[ipad(p)])];
-                if (p >= 1 && c != cp) Rrun |= 1u << i;
-                cp = c;
-            }
-        }
-    }
     int64_t wbase = 0;
     for (int k = 0; k < w; ++k) wbase += h.wtot[k];
     const int64_t Xf = wbase + winc - csum;
@@ -618,7 +654,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     // warm, the candidate runs with the points below their chords
     uint32_t B = 0;
     if (ids_prev) {
-        B = wsh::candidate_boundaries(h, tst, t, first, n, Rrun);
+        B = small_warm<T>(s, tst, ids_prev, a0, first, n);
     } else {
         int64_t dprev = devk(kprev);
 #pragma unroll
@@ -636,10 +672,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     if (converged) {
         st16[t] = (uint16_t)(B | (t == 0 ? 1u : 0u));
     } else {
-        if (!wsh::chain_tree_hull(h, tst, t, first, last, n, Xf, 1 << 30)) {   // (no cap: never fails)
-            if (t == 0) gen_list[atomicAdd(gen_count, 1)] = seg;
-            return;
-        }
+        small_chain_tree(h, tst, first, last, n, Xf);
         st16[t] = 0;
         __syncthreads();
         for (int k = h.lo[t]; k < (int)h.hi[t]; ++k) {
