@@ -237,7 +237,7 @@ void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max);
  * device-wide path runs first (appendix algorithm "Imminent collisions
  * algorithm (v2)"); a tile whose rounds have not converged within the cap
  * takes the tree of bridge merges instead.  0 skips the rounds (every tile
- * takes the merges); a negative value restores the default (24).  Takes
+ * takes the merges); a negative value restores the default (32).  Takes
  * effect on the next call.  Test and benchmark hook. */
 void ws_debug_set_ic_cap(ws_ctx* ctx, int cap);
 

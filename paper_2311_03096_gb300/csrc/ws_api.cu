@@ -28,7 +28,7 @@ struct ws_ctx {
     uint32_t* status = nullptr;   // device status word
     uint64_t spin_limit = WS_DEFAULT_SPIN;
     int64_t small_max_override = -1;
-    int ic_cap = 24;   // in-tile Imminent Collisions round cap
+    int ic_cap = 32;   // in-tile Imminent Collisions round cap
     std::vector<PlanCacheEntry> cache;
     std::mutex mu;
     WsProf prof;
@@ -684,7 +684,7 @@ void ws_debug_set_spin_limit(ws_ctx* ctx, int64_t limit) {
 
 void ws_debug_set_ic_cap(ws_ctx* ctx, int cap) {
     if (!ctx) return;
-    ctx->ic_cap = cap < 0 ? 24 : cap;
+    ctx->ic_cap = cap < 0 ? 32 : cap;
 }
 
 ws_status ws_debug_hull_stats(ws_ctx* ctx, int64_t d, ws_dtype dtype, int64_t* counts, int n_counts) {

@@ -93,6 +93,14 @@ struct FastSmem {
 // When a round removes nothing every adjacent pair of blocks has increasing
 // means: the blocks are the tile's pool-adjacent-violators partition, and
 // their boundaries (with points 0 and n) its hull vertices.
+// The hull by chains and trees for a tile whose rounds hit the cap: out of
+// line (rare), so that the rounds' code stays compact in the instruction
+// cache.  All threads call it; false if a CTA-level bridge walk hit its cap.
+__device__ __noinline__ bool tile_chain_tree(wsh::Smem& s, const wsh::Test& tst, int first, int last, int n,
+                                             int64_t Xf) {
+    return wsh::chain_tree_hull(s, tst, threadIdx.x, first, last, n, Xf, CTA_WALK_CAP);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K* __restrict__ sorted,
                                                    const TileDesc* __restrict__ htiles,
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
     if (converged) {
         c = __popc(B) + (t == 0 ? 1 : 0) + (first < n && last == n ? 1 : 0);
     } else {
-        if (!wsh::chain_tree_hull(s, tst, t, first, last, n, Xf, CTA_WALK_CAP)) {
+        if (!tile_chain_tree(s, tst, first, last, n, Xf)) {
             if (t == 0) { gen_list[atomicAdd(gen_count, 1)] = tile; tile_rounds[tile] = -2; }
             return;
         }
