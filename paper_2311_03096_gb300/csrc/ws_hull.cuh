@@ -668,15 +668,17 @@ __device__ __forceinline__ bool ic_rounds(Smem& s, const Test& T, int t, int fir
 // Warm start from a candidate partition given as runs of points (the paper's
 // Future Work: start from a candidate weight-sharing and edit it into the
 // exact one).  R: this lane's run boundaries (bit i = point first + i).
-// Returns R plus every interior point of a run that lies strictly below the
-// chord of its run.  A vertex of the lower hull lies strictly below every
-// chord that spans it, so the result holds every hull vertex whatever the runs
-// are, and the Imminent Collisions rounds started from it remove the rest:
-// the runs only change the time, never the partition.  Prefix sums of every
+// G: the points that survive round 1 (gap test; every hull vertex does).
+// Returns the run boundaries in G plus every interior point of a run, in G,
+// that lies strictly below the chord of its run.  A vertex of the lower hull
+// lies strictly below every chord that spans it, so the result holds every
+// hull vertex whatever the runs are, and the Imminent Collisions rounds
+// started from it remove the rest: the runs only change the time, never the
+// partition.  Prefix sums of every
 // point must be in s.X (the barrier here publishes them).  All threads call
 // this.
 __device__ __forceinline__ uint32_t candidate_boundaries(Smem& s, const Test& T, int t, int first, int n,
-                                                         uint32_t R) {
+                                                         uint32_t R, uint32_t G) {
     const int BIG = 1 << 20;
     const Around ar = around(s, t, first, R, 0u);
     const int pS = ar.pS, nS = ar.nS;
@@ -687,7 +689,7 @@ __device__ __forceinline__ uint32_t candidate_boundaries(Smem& s, const Test& T,
         const int lo = first < 1 ? 1 : first, hi = min(first + M, n);   // points [lo, hi)
         if (hi > lo) bits = (0xffffffffu >> (32 - (hi - lo))) << (lo - first);
     }
-    bits &= ~R;
+    bits &= ~R & G;
     uint32_t F = 0;
     while (bits) {
         const int i = __ffs((int)bits) - 1;
@@ -698,7 +700,7 @@ __device__ __forceinline__ uint32_t candidate_boundaries(Smem& s, const Test& T,
         const int c = above ? first + __ffs((int)above) - 1 : nextS;
         if (T(a, xat(s, a), p, xat(s, p), c, xat(s, c))) F |= 1u << i;
     }
-    return R | F;
+    return (R & G) | F;
 }
 
 // The tile's hull by per-lane chains (stack form of pool-adjacent-violators),

@@ -299,6 +299,7 @@ struct LeanSmem {
     uint32_t starts[wsh::TILE / 32 + 1];   // bit p: a cluster starts at sorted position p
     TileScale ts;
     SegConst sc;    // the segment's global fixed-point scale (cluster values)
+    int64_t t11;    // round-1 gap threshold (tile units)
     int flags, emin;
 };
 
@@ -349,13 +350,14 @@ __device__ __noinline__ void small_chain_tree(wsh::Smem& h, const wsh::Test& tst
 }
 
 // Warm start: the runs of equal earlier cluster ids (low 16 bits; any values
-// are valid) along the sorted order, then candidate_boundaries.  The earlier
+// are valid) along the sorted order, then candidate_boundaries on the
+// round-1 survivors G.  The earlier
 // ids are staged by original position in `cprev` (the keys' storage: the
 // keys are in registers by now).  Prefix sums of every point must be written
 // (the barriers here publish them).
 template <typename T>
 __device__ __noinline__ uint32_t small_warm(LeanSmem<T>& s, const wsh::Test& tst, const int32_t* ids_prev,
-                                            int64_t a0, int first, int n) {
+                                            int64_t a0, int first, int n, uint32_t G) {
     constexpr int M = wsh::M;
     const int t = threadIdx.x;
     uint16_t* cprev = reinterpret_cast<uint16_t*>(s.kv.keys);
@@ -389,7 +391,7 @@ __device__ __noinline__ uint32_t small_warm(LeanSmem<T>& s, const wsh::Test& tst
             }
         }
     }
-    return wsh::candidate_boundaries(s.u.h, tst, t, first, n, R);
+    return wsh::candidate_boundaries(s.u.h, tst, t, first, n, R, G);
 }
 
 template <typename T>
@@ -620,6 +622,9 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
         ts.fast = f ? 1 : 0;
         if (ts.sc.mlam == 0) { ts.modd = 0; ts.sodd = 0; }
         else { const int tz = __ffsll((long long)ts.sc.mlam) - 1; ts.modd = ts.sc.mlam >> tz; ts.sodd = ts.sc.s + tz; }
+        // lower bound of floor(2 mu) (muq is within 1e-6 relative of mu)
+        const float m2 = 2.0f * ts.muq * (1.0f - 1.0e-6f);
+        s.t11 = !f ? (int64_t)-1 : (m2 < 3.9e18f ? (int64_t)floorf(m2) - 1 : (int64_t)3.9e18);
         h.general = 0;
     }
     auto devk = [&](K k) -> int64_t {
@@ -649,22 +654,26 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     tst.P.thr = nullptr;
     tst.P.modd = s.ts.modd;
     tst.P.sodd = s.ts.sodd;
-    // round 1 of the Imminent Collisions rounds: boundaries where neighbours do
-    // not collide (the hull test on the consecutive points p-1, p, p+1); or,
-    // warm, the candidate runs with the points below their chords
+    // round 1 of the Imminent Collisions rounds: point p stays a boundary iff
+    // y_{p-1} < y_p, i.e. the gap x_p - x_{p-1} exceeds 2 lambda/(d-1) = 2 mu.
+    // t11 is a lower bound of floor(2 mu) in tile units, so a few points at
+    // the threshold may stay too: a superset of the hull vertices is all the
+    // rounds need (their first round tests every boundary exactly).  Warm:
+    // of these, the candidate's run boundaries and the points below their
+    // run's chord.
     uint32_t B = 0;
-    if (ids_prev) {
-        B = small_warm<T>(s, tst, ids_prev, a0, first, n);
-    } else {
+    {
+        const int64_t t11 = s.t11;
         int64_t dprev = devk(kprev);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const int p = first + i;
             const int64_t di = dev(i);
-            if (p >= 1 && p < n && tst(p - 1, 0, p, dprev, p + 1, dprev + di)) B |= 1u << i;
+            if (p >= 1 && p < n && di - dprev > t11) B |= 1u << i;
             dprev = di;
         }
     }
+    if (ids_prev) B = small_warm<T>(s, tst, ids_prev, a0, first, n, B);
     int rounds = 0;
     bool converged = false;
     if (ic_cap > 0) converged = wsh::ic_rounds(h, tst, t, first, n, B, ic_cap, rounds);
