@@ -11,6 +11,8 @@
 // 6144 keys by digit in shared memory, publishes its per-digit counts, gets
 // the counts of the earlier tiles of the same segment through a decoupled
 // look-back (bounded waits), and writes its keys as per-digit contiguous runs.
+#include <algorithm>
+
 #include "ws_kernels.cuh"
 
 namespace {
@@ -38,10 +40,14 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
 
 // Also the smallest effective exponent of a nonzero value of each segment
 // (seg_emin, reduced with atomicMin; cleared to INT_MAX before the launch),
-// which fixes the segment's fixed-point scale.
+// which fixes the segment's fixed-point scale.  A persistent grid: each CTA
+// walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... (increasing, so it
+// meets each segment in one run) and adds its shared-memory counts to the
+// segment's global histogram once per segment, not once per tile.
 template <typename T>
 __global__ void __launch_bounds__(WS_SORT_NT) k_hist(const T* __restrict__ values, const TileDesc* __restrict__ tiles,
-                                                     uint32_t* hist, int32_t* seg_emin, uint32_t* status) {
+                                                     int n_tiles, uint32_t* hist, int32_t* seg_emin,
+                                                     uint32_t* status) {
     typedef KeyOf<T> KO;
     constexpr int P = KO::BITS / 8;
     __shared__ uint32_t h[P * 256];
@@ -49,7 +55,6 @@ __global__ void __launch_bounds__(WS_SORT_NT) k_hist(const T* __restrict__ value
     for (int i = threadIdx.x; i < P * 256; i += WS_SORT_NT) h[i] = 0;
     if (threadIdx.x == 0) s_emin = 0x7fffffff;
     __syncthreads();
-    const TileDesc td = tiles[blockIdx.x];
     bool bad = false;
     int emin = 0x7fffffff;
     auto count = [&](T v) {
@@ -59,32 +64,49 @@ __global__ void __launch_bounds__(WS_SORT_NT) k_hist(const T* __restrict__ value
 #pragma unroll
         for (int p = 0; p < P; ++p) atomicAdd(&h[p * 256 + (int)((k >> (8 * p)) & 0xff)], 1u);
     };
-    const T* src = values + td.vpos;
+    auto flush = [&](int lseg) {   // (all threads; ends with zero counts)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+        if ((threadIdx.x & 31) == 0 && emin != 0x7fffffff) atomicMin(&s_emin, emin);
+        emin = 0x7fffffff;
+        __syncthreads();
+        if (threadIdx.x == 0 && s_emin != 0x7fffffff) atomicMin(&seg_emin[lseg], s_emin);
+        uint32_t* gh = hist + (size_t)lseg * P * 256;
+        for (int i = threadIdx.x; i < P * 256; i += WS_SORT_NT) {
+            if (h[i]) atomicAdd(&gh[i], h[i]);
+            h[i] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_emin = 0x7fffffff;
+        __syncthreads();
+    };
     constexpr int VEC = 16 / (int)sizeof(T);                  // values per 16-byte load
     constexpr int NV = WS_SORT_TILE / (WS_SORT_NT * VEC);     // 16-byte loads per thread
-    if (td.len == WS_SORT_TILE && (((uintptr_t)src) & 15) == 0) {
-        // whole, aligned tile: every load issued before the first count
-        uint4 buf[NV];
-#pragma unroll
-        for (int j = 0; j < NV; ++j) buf[j] = __ldcs(reinterpret_cast<const uint4*>(src) + j * WS_SORT_NT + threadIdx.x);
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            const T* e = reinterpret_cast<const T*>(&buf[j]);
-#pragma unroll
-            for (int u = 0; u < VEC; ++u) count(e[u]);
+    int cur = -1;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const TileDesc td = tiles[tile];
+        if (td.lseg != cur) {
+            if (cur >= 0) flush(cur);
+            cur = td.lseg;
         }
-    } else {
-        for (int i = threadIdx.x; i < td.len; i += WS_SORT_NT) count(src[i]);
-    }
-    if (bad) ws_flag(status, WS_STATUS_NONFINITE);
+        const T* src = values + td.vpos;
+        if (td.len == WS_SORT_TILE && (((uintptr_t)src) & 15) == 0) {
+            // whole, aligned tile: every load issued before the first count
+            uint4 buf[NV];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
-    if ((threadIdx.x & 31) == 0 && emin != 0x7fffffff) atomicMin(&s_emin, emin);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_emin != 0x7fffffff) atomicMin(&seg_emin[td.lseg], s_emin);
-    uint32_t* gh = hist + (size_t)td.lseg * P * 256;
-    for (int i = threadIdx.x; i < P * 256; i += WS_SORT_NT)
-        if (h[i]) atomicAdd(&gh[i], h[i]);
+            for (int j = 0; j < NV; ++j) buf[j] = __ldcs(reinterpret_cast<const uint4*>(src) + j * WS_SORT_NT + threadIdx.x);
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                const T* e = reinterpret_cast<const T*>(&buf[j]);
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) count(e[u]);
+            }
+        } else {
+            for (int i = threadIdx.x; i < td.len; i += WS_SORT_NT) count(src[i]);
+        }
+    }
+    if (cur >= 0) flush(cur);
+    if (bad) ws_flag(status, WS_STATUS_NONFINITE);
 }
 
 // exclusive scan of every (segment, pass) histogram, in place
@@ -270,8 +292,20 @@ cudaError_t ws_large_sort(const LargeWork<T>& W, const T* values, uint32_t* stat
     if (e) return e;
     e = cudaMemsetAsync(W.seg_emin, 0x7f, sizeof(int32_t) * (size_t)W.n_lseg, st);
     if (e) return e;
+    // the histogram's persistent grid: every CTA resident at once
+    static const int hist_grid = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hist<T>, WS_SORT_NT, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 2 * 152;
+        }
+        return std::max(1, sms * std::max(per_sm, 1));
+    }();
     WS_LAUNCH(W.prof, WSK_HIST, st,
-              (k_hist<T><<<W.n_sort_tiles, WS_SORT_NT, 0, st>>>(values, W.sort_tiles, W.hist, W.seg_emin, status)));
+              (k_hist<T><<<W.n_sort_tiles < hist_grid ? W.n_sort_tiles : hist_grid, WS_SORT_NT, 0, st>>>(
+                  values, W.sort_tiles, W.n_sort_tiles, W.hist, W.seg_emin, status)));
     WS_LAUNCH(W.prof, WSK_HIST_SCAN, st, (k_hist_scan<<<W.n_lseg * P, 256, 0, st>>>(W.hist, W.epoch)));
     size_t smem = ws_onesweep_smem<T>();
     e = cudaFuncSetAttribute(k_onesweep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
