@@ -299,8 +299,10 @@ def bench_batched(ws, ctx, stream, peak, reps=5):
             entry["graph_elements_per_s"] = sub_off[-1] / (msg / 1e3)
             entry["graph"] = byte_fracs(e_small, e_large, msg, peak)
             tuned = ws.Plan.autotuned(sub_off, v, lt, "fp32comp", thresholds=[0, 1024, 2048, 4096], reps=2, ctx=ctx)
-            entry["autotune"] = {"threshold": tuned.threshold,
-                                 "ms_by_threshold": dict(zip(["0", "1024", "2048", "4096"], tuned.times_ms))}
+            entry["autotune"] = {"threshold": tuned.threshold, "ic_cap": tuned.ic_cap,
+                                 "ms_by_threshold": dict(zip(["0", "1024", "2048", "4096"], tuned.times_ms)),
+                                 "tuned": "one-CTA length threshold, then the Imminent Collisions round cap "
+                                          "(8/16/32/64) on the chosen plan"}
             del tuned
             ctx.check(what="bench batched")
             out_h, ids_h = out.cpu().numpy(), ids.cpu().numpy()

@@ -103,7 +103,9 @@ void ws_plan_destroy(ws_plan* plan);
  * cluster_ids, prec) are timed with CUDA events on `stream` after one
  * warm-up; the fastest plan is returned in *plan and the others destroyed.
  * *chosen (nullable) receives its threshold, times_ms (nullable, n_cand
- * doubles) each candidate's mean milliseconds.  A set-up step: it allocates
+ * doubles) each candidate's mean milliseconds.  The chosen plan then times
+ * the round caps {8, 16, 32, 64} the same way and keeps the fastest
+ * (ws_plan_params reports it).  A set-up step: it allocates
  * and synchronises the stream, so it is not capturable.  Arguments as for
  * ws_plan_create and ws_prox_batched; reps >= 1, thresholds >= 0, else
  * WS_ERR_INVALID.  Not in the paper: a library convenience. */
@@ -111,6 +113,14 @@ ws_status ws_plan_autotune(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, 
                            const void* values, const double* lambdas, void* out, int32_t* cluster_ids,
                            ws_prec prec, const int64_t* thresholds, int n_cand, int reps, int64_t* chosen,
                            double* times_ms, void* stream);
+
+/* The parameters a plan runs with: its one-CTA length threshold and the round
+ * cap of the Imminent Collisions rounds (Sec. 4) in its tile and one-CTA
+ * kernels.  ws_plan_autotune times caps {8, 16, 32, 64} on its chosen plan
+ * after the thresholds and keeps the fastest for that plan; other plans use
+ * the context's cap (ws_debug_set_ic_cap).  Nullable outputs;
+ * WS_ERR_INVALID for a NULL plan. */
+ws_status ws_plan_params(const ws_plan* plan, int64_t* small_max, int* ic_cap);
 
 /* Batched forward (Alg. 2 per segment, lambda = lambdas[s] from DEVICE memory,
  * n_seg doubles, each >= 0 and finite -- checked on the device, reported as
@@ -234,11 +244,13 @@ void ws_debug_set_spin_limit(ws_ctx* ctx, int64_t limit);
 void ws_debug_set_small_max(ws_ctx* ctx, int64_t small_max);
 
 /* Round cap of the Imminent Collisions rounds that every hull tile of the
- * device-wide path runs first (appendix algorithm "Imminent collisions
- * algorithm (v2)"); a tile whose rounds have not converged within the cap
- * takes the tree of bridge merges instead.  0 skips the rounds (every tile
- * takes the merges); a negative value restores the default (32).  Takes
- * effect on the next call.  Test and benchmark hook. */
+ * device-wide path and every one-CTA segment runs first (appendix algorithm
+ * "Imminent collisions algorithm (v2)"); a tile whose rounds have not
+ * converged within the cap takes the tree of bridge merges instead.  0 skips
+ * the rounds (every tile takes the merges); a negative value restores the
+ * default (32).  Takes effect on the next call of every plan of the context
+ * except autotuned plans that chose their own cap (ws_plan_params).  Test and
+ * benchmark hook. */
 void ws_debug_set_ic_cap(ws_ctx* ctx, int cap);
 
 /* How the hull tiles of the last ws_prox call for (d, dtype) on this context

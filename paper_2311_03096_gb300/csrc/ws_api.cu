@@ -43,6 +43,7 @@ struct ws_plan {
     int64_t small_max = 0;
     bool sort_only = false;   // no one-CTA segments: everything takes the device-wide path
     int64_t small_force = -1; // >= 0: this plan's one-CTA length threshold (autotuned plans)
+    int ic_cap = -1;          // >= 0: this plan's round cap (autotuned plans), else the context's
     std::vector<int64_t> h_offsets;
     int64_t* d_offsets = nullptr;
     int32_t* d_small = nullptr;
@@ -135,7 +136,7 @@ LargeWork<T> make_work(const ws_plan* p) {
     W.tile_base = p->tile_base;
     W.scales = p->scales;
     W.tile_rounds = p->tile_rounds;
-    W.ic_cap = p->ctx->ic_cap;
+    W.ic_cap = p->ic_cap >= 0 ? p->ic_cap : p->ctx->ic_cap;
     W.seg_total = p->seg_total;
     W.seg_below = p->seg_below;
     W.rt = p->rt;
@@ -331,7 +332,7 @@ ws_status run_forward(ws_plan* p, const void* values, const double* lambdas, voi
     if (!fork(p, st, &ss)) return WS_ERR_CUDA;
     cudaError_t e = ws_launch_small<T>((const T*)values, p->d_offsets, p->d_small, p->n_small, lambdas, (T*)out, ids,
                                        n_clusters, fp64, ep, p->ctx->status, ss, &p->ctx->prof, p->small_gen,
-                                       p->small_gen_count, p->ctx->ic_cap, ids_prev);
+                                       p->small_gen_count, p->ic_cap >= 0 ? p->ic_cap : p->ctx->ic_cap, ids_prev);
     if (e) { join(p, st); return map_cuda(e); }
     if (p->n_lseg > 0) {
         LargeWork<T> W = make_work<T>(p);
@@ -630,11 +631,39 @@ ws_status ws_plan_autotune(ws_ctx* ctx, ws_plan** plan, const int64_t* offsets, 
             ws_plan_destroy(p);
         }
     }
+    // second stage: the round cap of the Imminent Collisions rounds, on the
+    // chosen plan (a runtime parameter of the tile and one-CTA kernels)
+    static const int kCaps[] = {8, 16, 32, 64};
+    if (rc == WS_OK && best) {
+        int best_cap = -1;
+        float cap_ms = best_ms;
+        for (int c = 0; c < 4 && rc == WS_OK; ++c) {
+            best->ic_cap = kCaps[c];
+            rc = ws_prox_batched(best, values, lambdas, out, cluster_ids, nullptr, prec, stream);   // warm-up
+            float ms = 0.0f;
+            if (rc == WS_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = WS_ERR_CUDA;
+            for (int r = 0; r < reps && rc == WS_OK; ++r)
+                rc = ws_prox_batched(best, values, lambdas, out, cluster_ids, nullptr, prec, stream);
+            if (rc == WS_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = WS_ERR_CUDA;
+            ms /= (float)reps;
+            if (rc == WS_OK && ms < cap_ms) { cap_ms = ms; best_cap = kCaps[c]; }
+        }
+        best->ic_cap = best_cap;   // -1: the context's cap was at least as fast
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) { cudaGetLastError(); if (best) ws_plan_destroy(best); return rc; }
     *plan = best;
     if (chosen) *chosen = best_t;
+    return WS_OK;
+}
+
+ws_status ws_plan_params(const ws_plan* plan, int64_t* small_max, int* ic_cap) {
+    if (!plan) return WS_ERR_INVALID;
+    if (small_max) *small_max = plan->small_max;
+    if (ic_cap) *ic_cap = plan->ic_cap >= 0 ? plan->ic_cap : plan->ctx->ic_cap;
     return WS_OK;
 }
 

@@ -55,6 +55,7 @@ def _load():
             lib.ws_plan_destroy.restype = None
             lib.ws_prox_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
             lib.ws_prox_batched_warm.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+            lib.ws_plan_params.argtypes = [_vp, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int)]
             lib.ws_prox.argtypes = [_vp, _vp, _i64, ctypes.c_double, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp]
             lib.ws_R.argtypes = [_vp, _vp, _i64, ctypes.c_int, _vp, _vp, _vp]
             lib.ws_prox_dlambda_batched.argtypes = [_vp, _vp, _vp, _vp, _vp]
@@ -333,6 +334,9 @@ class Plan:
         self.handle = h
         self.threshold = int(chosen.value)
         self.times_ms = times.tolist()
+        sm, cap = ctypes.c_int64(-1), ctypes.c_int(-1)
+        _check(_load().ws_plan_params(h, ctypes.byref(sm), ctypes.byref(cap)), "ws_plan_params")
+        self.ic_cap = int(cap.value)
         return self
 
     def forward(self, values: torch.Tensor, lambdas: torch.Tensor, prec: str = "fp32comp", ids: bool = True,

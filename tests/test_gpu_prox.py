@@ -226,6 +226,7 @@ def test_autotuned_plan_matches_default(ws, ctx):
     tuned = ws.Plan.autotuned(off, v, lt, "fp32comp", thresholds=[0, 1024, 4096], reps=2)
     ctx.check(what="autotune")
     assert tuned.threshold in (0, 1024, 4096) and len(tuned.times_ms) == 3 and min(tuned.times_ms) > 0
+    assert tuned.ic_cap in (8, 16, 32, 64)   # the cap it chose (or the context's default, 32)
     a = ws.Plan(off, torch.float32).forward(v, lt, "fp32comp")
     b = tuned.forward(v, lt, "fp32comp")
     ctx.check(what="autotuned forward")
