@@ -644,7 +644,6 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     for (int k = 0; k < w; ++k) wbase += h.wtot[k];
     const int64_t Xf = wbase + winc - csum;
     const int last = min(first + M, n);
-    if (first < n) wsh::lane_prefix(h, first, last, Xf, dev);
     wsh::Test tst;
     tst.sc = s.ts.sc;
     tst.P.s64 = nullptr;
@@ -661,16 +660,21 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     // rounds need (their first round tests every boundary exactly).  Warm:
     // of these, the candidate's run boundaries and the points below their
     // run's chord.
+    // (with the prefix sums of this lane's points: one pass over its deviations)
     uint32_t B = 0;
-    {
+    if (first < n) {
         const int64_t t11 = s.t11;
-        int64_t dprev = devk(kprev);
+        int64_t dprev = devk(kprev), X = Xf;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const int p = first + i;
-            const int64_t di = dev(i);
-            if (p >= 1 && p < n && di - dprev > t11) B |= 1u << i;
-            dprev = di;
+            if (p < n) {
+                const int64_t di = dev(i);
+                X += di;
+                wsh::xref(h, p + 1) = X;
+                if (p >= 1 && di - dprev > t11) B |= 1u << i;
+                dprev = di;
+            }
         }
     }
     if (ids_prev) B = small_warm<T>(s, tst, ids_prev, a0, first, n, B);
