@@ -497,6 +497,22 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
         if (l == 0) { ws_atomic_min_k(&s.kmin, lo); ws_atomic_max_k(&s.kmax, hi); }
     }
     __syncthreads();
+    // ---- the fixed point of the segment, from its extreme keys (the first and
+    // last sorted ones): a segment whose prefix sums need more than 64 bits
+    // goes to the general kernel before any sorting
+    const K kfirst = s.kmin, klast = s.kmax;
+    const T xlo = KO::from_key(kfirst), xhi = KO::from_key(klast);
+    const int emax = ws_fix_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), s.emin);
+    int sh;
+    const bool bin = ws_tile_binade<T>(kfirst, klast, n, emax, sh);
+    const int64_t q0 = ws_fixed<T>(xlo, emax);
+    const uint64_t range = bin ? (uint64_t)(klast - kfirst) : (uint64_t)(ws_fixed<T>(xhi, emax) - q0);
+    const bool lean = ws_lean_x(range, n);   // prefix sums in 64 bits
+    const bool d64 = ws_lean_tile(range, n);  // every Delta too
+    if (!lean) {   // (uniform)
+        if (t == 0) gen_list[atomicAdd(gen_count, 1)] = seg;
+        return;
+    }
     bool radix = false;
     {
         int* cnt = s.u.bucket.cnt;
@@ -599,20 +615,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     K kr[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) kr[i] = (first + i < n) ? s.kv.keys[kpad(first + i)] : s.kv.keys[0];
-    const K kfirst = s.kv.keys[0], klast = s.kv.keys[kpad(n - 1)];
     const K kprev = (t > 0 && first < n) ? s.kv.keys[kpad(first - 1)] : kfirst;
-    const T xlo = KO::from_key(kfirst), xhi = KO::from_key(klast);
-    const int emax = ws_fix_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), s.emin);
-    int sh;
-    const bool bin = ws_tile_binade<T>(kfirst, klast, n, emax, sh);
-    const int64_t q0 = ws_fixed<T>(xlo, emax);
-    const uint64_t range = bin ? (uint64_t)(klast - kfirst) : (uint64_t)(ws_fixed<T>(xhi, emax) - q0);
-    const bool lean = ws_lean_x(range, n);   // prefix sums in 64 bits
-    const bool d64 = ws_lean_tile(range, n);  // every Delta too
-    if (!lean) {   // (uniform)
-        if (t == 0) gen_list[atomicAdd(gen_count, 1)] = seg;
-        return;
-    }
     if (t == 0) {   // (no FP64 on this critical path)
         s.sc = ws_seg_const_f(n, lam, KO::L_BASE - emax, fp64 != 0);
         TileScale& ts = s.ts;
