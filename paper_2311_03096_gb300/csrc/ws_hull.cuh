@@ -158,22 +158,6 @@ struct Test {
     }
 };
 
-// Prefix sums of the lane's chunk: X of points first+1 .. last (last =
-// min(first + M, n)) from Xf = X at point first and dev(i) = deviation of
-// element first + i (tile units).
-template <class Dev>
-__device__ __forceinline__ void lane_prefix(Smem& s, int first, int last, int64_t Xf, const Dev& dev) {
-    int64_t X = Xf;
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-        const int p = first + i + 1;
-        if (p <= last) {
-            X += dev(i);
-            xref(s, p) = X;
-        }
-    }
-}
-
 // Stack form of pool-adjacent-violators over the lane's chunk (points
 // first .. last, prefix sums already in s.X; Xf = X at point first), as a
 // rolled loop (small code).  Writes the stack; returns its depth.

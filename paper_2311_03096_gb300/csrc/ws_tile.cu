@@ -170,7 +170,6 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
     for (int k = 0; k < w; ++k) wbase += s.wtot[k];
     const int64_t Xf = wbase + winc - csum;   // tile-local X at point `first`
     const int last = min(first + M, n);
-    if (first < n) wsh::lane_prefix(s, first, last, Xf, dev);
 
     wsh::Test tst;
     tst.sc = S.ts.sc;
@@ -184,16 +183,21 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
 
     // ---- round 1: boundaries where consecutive elements do not collide.
     // Bit i of B stands for point first + i (1 <= point <= n - 1).
+    // (with the prefix sums of this lane's points: one pass over its deviations)
     uint32_t B = 0;
-    {
+    if (first < n) {
         const int64_t t11 = S.ts.t11;
-        int64_t dprev = devk(kprev);
+        int64_t dprev = devk(kprev), X = Xf;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const int p = first + i;
-            const int64_t di = dev(i);
-            if (p >= 1 && p < n && di - dprev > t11) B |= 1u << i;
-            dprev = di;
+            if (p < n) {
+                const int64_t di = dev(i);
+                X += di;
+                wsh::xref(s, p + 1) = X;
+                if (p >= 1 && di - dprev > t11) B |= 1u << i;
+                dprev = di;
+            }
         }
     }
     int rounds = 0;
