@@ -229,15 +229,28 @@ __global__ void __launch_bounds__(NT, 4) k_hull_fast(const typename KeyOf<T>::K*
         vxo[k] = (i128)p * (i128)q0 + (bin ? ((i128)xu << sh) : (i128)xu);
     };
     if (converged) {
-        int k = 0;
-        if (t == 0) put(k++, 0);
+        // the vertex points staged in the (idle) lane-stack storage, then both
+        // arrays written by consecutive threads at consecutive vertices
+        static_assert((wsh::M + 1) * wsh::NT >= wsh::TILE + 1, "every vertex has a staging slot");
+        uint16_t* stage = s.st;
+        int k = o;
+        if (t == 0) stage[k++] = 0;
         uint32_t rest = B;
         while (rest) {
             const int i = __ffs((int)rest) - 1;
             rest &= rest - 1;
-            put(k++, first + i);
+            stage[k++] = (uint16_t)(first + i);
         }
-        if (first < n && last == n) put(k++, n);
+        if (first < n && last == n) stage[k++] = (uint16_t)n;
+        __syncthreads();
+        i128* vxt = vx + (size_t)tile * (HT + 1);
+        uint16_t* vpt = vp + (size_t)tile * (HT + 1);
+        for (int i = t; i < nv; i += NT) {
+            const int p = stage[i];
+            const int64_t xu = wsh::xat(s, p);
+            vpt[i] = (uint16_t)p;
+            vxt[i] = (i128)p * (i128)q0 + (bin ? ((i128)xu << sh) : (i128)xu);
+        }
     } else {
         for (int k = 0; k < c; ++k) put(k, s.st[(lo + k) * NT + t]);
     }
