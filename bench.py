@@ -55,16 +55,19 @@ ONE_CTA_MAX_F32 = 4096   # FP32 segments up to this length run one CTA each
 MODEL_B = {"key_only_52B": 52, "index_payload_80B": 80}
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the bench's own workload, and the hash of the kernel sources it
-# was taken on; reported as null once the sources change (see profiles/).
-NCU_TRAFFIC = {}
-NCU_SOURCE_HASH = ""
+# ncu capture of the bench's own workload, and the hash of the source files the
+# kernel is built from when the counters were taken; reported as null once any
+# of them changes (see profiles/).
+NCU_SOURCES = {"onesweep": ["ws_sort.cu", "ws_kernels.cuh", "ws_block.cuh", "ws_common.cuh"]}
+NCU_TRAFFIC = {"onesweep": 511.7e6}   # d = 2^26, mean of the 4 passes (1 ncu pass each)
+NCU_SOURCE_HASH = {"onesweep": "7db8ecd60ede541e"}
 
 
-def source_hash() -> str:
+def source_hash(files=None) -> str:
+    """Hash of the kernel sources (all of csrc/, or the listed files of it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_03096_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in sorted(files if files is not None else os.listdir(csrc)):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -554,7 +557,9 @@ def main():
     if dom is not None:
         ms_avg = kern[dom][0] / kern[dom][1]
         per_launch = ALGO_BYTES_PER_ELEM_F32.get(dom)
-        traffic = NCU_TRAFFIC.get(dom) if NCU_SOURCE_HASH == source_hash() else None
+        traffic = None
+        if dom in NCU_TRAFFIC and NCU_SOURCE_HASH.get(dom) == source_hash(NCU_SOURCES.get(dom)):
+            traffic = NCU_TRAFFIC[dom]
         if per_launch is not None:
             achieved = per_launch * args.d / (ms_avg / 1e3) / 1e9
             roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
