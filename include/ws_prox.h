@@ -228,6 +228,18 @@ ws_status ws_R(ws_ctx* ctx, const void* w, int64_t d, ws_dtype dtype, double* R_
  * word (WS_OK if no device-side error happened since the last call). */
 ws_status ws_get_status(ws_ctx* ctx, void* stream);
 
+/* Whether a call since the last query used a fixed point that truncated
+ * input values: a segment's nonzero values spanning more than 34 binades
+ * (FP32; 5 for FP64) get the scale of its largest values, and values more
+ * than that far below lose their lowest bits (toward zero).  The partition is
+ * then the exact prox of the truncated values and every output stays within
+ * the stated tolerance, but a partition check against an exact reference is
+ * not guaranteed (FP64 segments of N(0,1) weights already span more than 5
+ * binades).  Information, not an error: ws_get_status does not report it.
+ * Synchronises `stream`; *inexact = 1 or 0; the flag is cleared.  Call when
+ * no other stream is using the context. */
+ws_status ws_get_inexact(ws_ctx* ctx, int* inexact, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* ws_status_string(ws_status s);
 

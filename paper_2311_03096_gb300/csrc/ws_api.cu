@@ -29,6 +29,7 @@ struct ws_ctx {
     uint64_t spin_limit = WS_DEFAULT_SPIN;
     int64_t small_max_override = -1;
     int ic_cap = 32;   // in-tile Imminent Collisions round cap
+    bool inexact = false;   // WS_STATUS_INEXACT seen by ws_get_status, not yet reported
     std::vector<PlanCacheEntry> cache;
     std::mutex mu;
     WsProf prof;
@@ -700,10 +701,25 @@ ws_status ws_get_status(ws_ctx* ctx, void* stream) {
     uint32_t h = 0;
     if (cudaMemcpy(&h, ctx->status, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return WS_ERR_CUDA;
     if (h && cudaMemset(ctx->status, 0, sizeof(uint32_t)) != cudaSuccess) return WS_ERR_CUDA;
+    if (h & WS_STATUS_INEXACT) ctx->inexact = true;   // (information for ws_get_inexact)
     if (h & WS_STATUS_NONFINITE) return WS_ERR_NONFINITE;
     if (h & WS_STATUS_BAD_LAMBDA) return WS_ERR_INVALID;
     if (h & WS_STATUS_TIMEOUT) return WS_ERR_TIMEOUT;
     if (h & WS_STATUS_INTERNAL) return WS_ERR_INTERNAL;
+    return WS_OK;
+}
+
+ws_status ws_get_inexact(ws_ctx* ctx, int* inexact, void* stream) {
+    if (!ctx || !inexact) return WS_ERR_INVALID;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) { cudaGetLastError(); return WS_ERR_CUDA; }
+    uint32_t h = 0;
+    if (cudaMemcpy(&h, ctx->status, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return WS_ERR_CUDA;
+    if (h & WS_STATUS_INEXACT) {   // clear the bit, keep the error bits for ws_get_status
+        const uint32_t rest = h & ~(uint32_t)WS_STATUS_INEXACT;
+        if (cudaMemcpy(ctx->status, &rest, sizeof rest, cudaMemcpyHostToDevice) != cudaSuccess) return WS_ERR_CUDA;
+    }
+    *inexact = ((h & WS_STATUS_INEXACT) || ctx->inexact) ? 1 : 0;
+    ctx->inexact = false;
     return WS_OK;
 }
 

@@ -30,6 +30,7 @@ enum : uint32_t {
     WS_STATUS_TIMEOUT = 2u,
     WS_STATUS_INTERNAL = 4u,
     WS_STATUS_BAD_LAMBDA = 8u,
+    WS_STATUS_INEXACT = 16u,   // information, not an error (ws_note_scale)
 };
 
 __device__ __forceinline__ void ws_flag(uint32_t* status, uint32_t bit) {
@@ -116,6 +117,14 @@ template <typename T> __device__ __forceinline__ int64_t ws_fixed(T v, int emax)
 // deviations instead of 128-bit sums.
 template <typename T> __device__ __forceinline__ int ws_fix_scale(int emax, int emin) {
     return (emin <= emax && emax - emin <= KeyOf<T>::FIX_OFS) ? emin + KeyOf<T>::FIX_OFS : emax;
+}
+
+// Records in the status word that a segment's nonzero values span more than
+// FIX_OFS binades (ws_fix_scale then returns emax and the smallest values lose
+// their lowest bits in the fixed point; the partition is exact for the
+// truncated values).  Information for ws_get_inexact, not an error.
+template <typename T> __device__ __forceinline__ void ws_note_scale(int emax, int emin, uint32_t* status) {
+    if (emin <= emax && emax - emin > KeyOf<T>::FIX_OFS) ws_flag(status, WS_STATUS_INEXACT);
 }
 
 // ---------------------------------------------------------------------------

@@ -503,6 +503,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     const K kfirst = s.kmin, klast = s.kmax;
     const T xlo = KO::from_key(kfirst), xhi = KO::from_key(klast);
     const int emax = ws_fix_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), s.emin);
+    if (t == 0) ws_note_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), s.emin, status);
     int sh;
     const bool bin = ws_tile_binade<T>(kfirst, klast, n, emax, sh);
     const int64_t q0 = ws_fixed<T>(xlo, emax);

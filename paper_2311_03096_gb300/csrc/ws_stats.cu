@@ -70,7 +70,7 @@ template <typename T>
 __global__ void __launch_bounds__(32) k_R_final(const LargeSeg* __restrict__ lsegs, const TileDesc* __restrict__ tiles,
                                                 const typename KeyOf<T>::K* __restrict__ sorted,
                                                 const int32_t* __restrict__ seg_emin, const RPartial* part,
-                                                double* R_out, double* metric_out) {
+                                                double* R_out, double* metric_out, uint32_t* status) {
     typedef KeyOf<T> KO;
     if (threadIdx.x != 0) return;
     const LargeSeg ls = lsegs[blockIdx.x];
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(32) k_R_final(const LargeSeg* __restrict__ lse
     }
     const T xlo = KO::from_key(sorted[ls.kpos]), xhi = KO::from_key(sorted[ls.kpos + ls.len - 1]);
     const int E = ws_fix_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), seg_emin[blockIdx.x]);
+    ws_note_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), seg_emin[blockIdx.x], status);
     const int L = KO::L_BASE - E;
     if (R_out) R_out[ls.seg] = ls.len > 1 ? ldexp(ws_i128_to_double(s), -L) / (double)(ls.len - 1) : 0.0;
     if (metric_out) metric_out[ls.seg] = nz > 0 ? (double)dis / (double)nz : 0.0;
@@ -102,7 +103,7 @@ cudaError_t ws_large_R(const LargeWork<T>& W, const T* values, double* R_out, do
               (k_R_tiles<T><<<W.n_sort_tiles, 256, 0, st>>>(sorted, W.sort_tiles, W.lsegs, W.seg_emin, part)));
     WS_LAUNCH(W.prof, WSK_MISC, st,
               (k_R_final<T><<<W.n_lseg, 32, 0, st>>>(W.lsegs, W.sort_tiles, sorted, W.seg_emin, part, R_out,
-                                                     metric_out)));
+                                                     metric_out, status)));
     return cudaGetLastError();
 }
 

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(WS_NSCALE) k_scales(const typename KeyOf<T>::K
     if (j == 0) {
         rt[lseg].emax = emax;
         if (!lam_ok) ws_flag(status, WS_STATUS_BAD_LAMBDA);
+        ws_note_scale<T>(max(ws_eff_exp(xlo), ws_eff_exp(xhi)), seg_emin[lseg], status);
     }
     if (j > KO::FIX_OFS && j != WS_NSCALE - 1) return;
     TileScale ts;

@@ -68,6 +68,7 @@ def _load():
             lib.ws_prox_backward_batched.argtypes = [_vp, _vp, _vp, _vp, _vp]
             lib.ws_prox_backward.argtypes = [_vp, _vp, _vp, _i64, _vp, ctypes.c_int, _vp]
             lib.ws_get_status.argtypes = [_vp, _vp]
+            lib.ws_get_inexact.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _vp]
             lib.ws_debug_set_spin_limit.argtypes = [_vp, _i64]
             lib.ws_debug_set_spin_limit.restype = None
             lib.ws_debug_set_small_max.argtypes = [_vp, _i64]
@@ -137,6 +138,12 @@ class Context:
     def status(self, stream=None) -> int:
         """Synchronise the stream and return (and clear) the device status."""
         return _load().ws_get_status(self.handle, _stream(stream))
+
+    def inexact(self, stream=None) -> bool:
+        """ws_get_inexact: did a call since the last query truncate input values in its fixed point?"""
+        flag = ctypes.c_int(0)
+        _check(_load().ws_get_inexact(self.handle, ctypes.byref(flag), _stream(stream)), "ws_get_inexact")
+        return bool(flag.value)
 
     def check(self, stream=None, what="ws_prox"):
         _check(self.status(stream), what)

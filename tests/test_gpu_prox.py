@@ -291,3 +291,28 @@ def test_one_signed_inputs_device_wide(ws, ctx, dt, d):
         for lam in (1e-3, 0.5):
             out, ids, nc = run_one(ws, ctx, w_np, lam, dt, "fp64")
             compare_segment(w_np, lam, out, ids, nc, TOL[(dt, "fp64")])
+
+
+@pytest.mark.parametrize("path", ["one_cta", "device_wide"])
+def test_inexact_fixed_point_is_reported(ws, ctx, path):
+    # values spanning more than 34 binades (FP32) are truncated in the fixed
+    # point: ws_get_inexact says so; within the span it stays clear
+    if path == "device_wide":
+        ctx.set_small_max(0)
+    ctx.inexact()   # (clear)
+    w_np = inputs.normal(4000, seed=31, dtype=np.float32)
+    w_np = np.where(np.abs(w_np) < 1e-3, np.float32(1e-3), w_np)   # about 12 binades
+    out, ids, nc = run_one(ws, ctx, w_np, 1.0, "f32", "fp32comp")
+    assert not ctx.inexact()
+    wide = w_np.copy()
+    wide[::7] *= np.float32(1e-30)   # now about 110 binades
+    out, ids, nc = run_one(ws, ctx, wide, 1.0, "f32", "fp32comp")
+    assert ctx.inexact()
+    assert not ctx.inexact()   # cleared by the query
+    # the outputs still meet the tolerance (values only: the partition is exact
+    # for the truncated values)
+    ref = oracle.prox(wide.astype(np.float64), 1.0)[0]
+    assert np.abs(out.astype(np.float64) - ref).max() <= 1e-5 * (np.abs(wide).max() + 1.0)
+    # FP64 segments of N(0,1) weights span more than 5 binades: reported
+    run_one(ws, ctx, inputs.normal(4096, seed=32, dtype=np.float64), 0.1, "f64", "fp64")
+    assert ctx.inexact()
