@@ -50,7 +50,7 @@ template <typename T>
 __device__ __forceinline__ T ws_bwd_mean(i128 S, int cnt, int emax) {
     const int Lg = BwdFix<T>::SH - emax + BwdFix<T>::BIAS + BwdFix<T>::MANT;
     if (sizeof(T) == 4) return (T)ldexpf(ws_i128_to_float_scaled(S, 0) / (float)cnt, -Lg);
-    return (T)ldexp(ws_i128_to_double(S) / (double)cnt, -Lg);
+    return (T)ldexp(ws_div_i128_n(S, cnt), -Lg);
 }
 
 __device__ __forceinline__ void ws_atomic_add_i128(unsigned long long* lo_hi, i128 v) {

@@ -307,6 +307,29 @@ __device__ __forceinline__ double ws_i128_to_double(i128 v) {
     return neg ? -r : r;
 }
 
+// S / n in FP64 arithmetic for an exact 128-bit sum S and a count n >= 1,
+// without an FP64 division (GB300 runs FP64 at a small fraction of the FP32
+// rate): q = the FP32 quotient (<= 4 roundings: |q - S/n| <= 2^-21 |S/n|),
+// truncated to an integer Q; the remainder R = S - Q n is exact in 128 bits
+// and |R / n| <= 2^-21 |S/n| + 1, so S/n = Q + R/n with R/n taken in FP32 has
+// an error below 2^-42 |S/n| + 2^-21 (in the units of S).
+__device__ __forceinline__ double ws_div_i128_n(i128 S, int64_t n) {
+    const float q = ws_i128_to_float_scaled(S, 0) / (float)n;
+    const uint32_t bits = __float_as_uint(q);
+    const int e = (int)((bits >> 23) & 0xffu) - 150;   // q = m 2^e, m the 24-bit significand
+    const uint32_t m = (bits & 0x7fffffu) | 0x800000u;
+    u128 mag = 0;
+    float qt = 0.0f;   // trunc(q), exactly Q
+    if (((bits >> 23) & 0xffu) >= 127u) {   // |q| >= 1
+        mag = e >= 0 ? ((u128)m << e) : (u128)(m >> (-e));
+        qt = truncf(q);
+    }
+    const i128 Q = (bits >> 31) ? -(i128)mag : (i128)mag;
+    const i128 R = S - Q * (i128)n;
+    const float corr = ws_i128_to_float_scaled(R, 0) / (float)n;
+    return (double)qt + (double)corr;
+}
+
 // Weight sharing + l1 with rewinding (Rewinding section, Alg. 2): a cluster
 // with mean position x and mean velocity v (its shift) ends at
 //   0                                  if |x + v| < beta,
@@ -333,7 +356,7 @@ template <> struct ValueOut<float> {
         int64_t n = b - a;
         int64_t t = sc.d - a - b;
         if (fp64) {
-            double mean = (n == 1) ? (double)xsingle : ldexp(ws_i128_to_double(SX) / (double)n, -sc.L);
+            double mean = (n == 1) ? (double)xsingle : ldexp(ws_div_i128_n(SX, n), -sc.L);
             return (float)ws_epilogue<double>(mean, sc.mu_d * (double)t, ep.beta, ep.gamma, ep.on != 0);
         }
         float mean = (n == 1) ? xsingle : ldexpf(ws_i128_to_float_scaled(SX, 0) / (float)n, -sc.L);
@@ -350,7 +373,7 @@ template <> struct ValueOut<double> {
             float mean = (n == 1) ? (float)xsingle : ldexpf(ws_i128_to_float_scaled(SX, 0) / (float)n, -sc.L);
             return (double)ws_epilogue<float>(mean, sc.mu_f * (float)t, ep.beta_f, ep.gamma_f, ep.on != 0);
         }
-        double mean = (n == 1) ? xsingle : ldexp(ws_i128_to_double(SX) / (double)n, -sc.L);
+        double mean = (n == 1) ? xsingle : ldexp(ws_div_i128_n(SX, n), -sc.L);
         return ws_epilogue<double>(mean, sc.mu_d * (double)t, ep.beta, ep.gamma, ep.on != 0);
     }
 };
