@@ -635,12 +635,17 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
         return bin ? (int64_t)(k - kfirst) : ws_fixed<T>(KO::from_key(k), emax) - q0;
     };
     auto dev = [&](int i) -> int64_t { return devk(kr[i]); };
+    // the deviations, once: their running sums (this lane's prefix sums
+    // relative to its first point) go straight into the prefix-sum slots (the
+    // sort's scratch is dead); the lane's offset is added below
     int64_t csum = 0;
 #pragma unroll
     for (int i = 0; i < M; ++i)
-        if (first + i < n) csum += dev(i);
+        if (first + i < n) {
+            csum += dev(i);
+            wsh::xref(h, first + i + 1) = csum;
+        }
     const int64_t winc = ws_warp_incl_scan<long long>((long long)csum);
-    __syncthreads();   // (the sort's scratch is dead: the hull's shared memory may be written)
     if (l == 31) h.wtot[w] = winc;
     if (t == 0) wsh::xref(h, 0) = 0;
     __syncthreads();
@@ -664,18 +669,20 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     // rounds need (their first round tests every boundary exactly).  Warm:
     // of these, the candidate's run boundaries and the points below their
     // run's chord.
-    // (with the prefix sums of this lane's points: one pass over its deviations)
+    // (with the lane's offset added to its prefix sums)
     uint32_t B = 0;
     if (first < n) {
         const int64_t t11 = s.t11;
-        int64_t dprev = devk(kprev), X = Xf;
+        int64_t dprev = devk(kprev), prevX = 0;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const int p = first + i;
             if (p < n) {
-                const int64_t di = dev(i);
-                X += di;
-                wsh::xref(h, p + 1) = X;
+                int64_t& slot = wsh::xref(h, p + 1);
+                const int64_t Xl = slot;
+                const int64_t di = Xl - prevX;   // the deviation of element p
+                prevX = Xl;
+                slot = Xl + Xf;
                 if (p >= 1 && di - dprev > t11) B |= 1u << i;
                 dprev = di;
             }
