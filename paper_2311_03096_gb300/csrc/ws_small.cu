@@ -303,6 +303,26 @@ struct LeanSmem {
     int flags, emin;
 };
 
+// Exclusive scan of one int per thread over the CTA with a single barrier:
+// every thread reads the warp totals itself.  wsum (one word per warp) must
+// not be written again before the next barrier of the caller.
+__device__ __forceinline__ int lean_excl_scan(int v, int* wsum, int* total) {
+    constexpr int NW = wsh::NT / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int inc = ws_warp_incl_scan<int>(v);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int base = 0, tot = 0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        const int x = wsum[k];
+        base += k < w ? x : 0;
+        tot += x;
+    }
+    *total = tot;
+    return base + inc - v;
+}
+
 __device__ __forceinline__ int lean_kpad(int p) { return p + (p >> 4); }          // keys, counts
 __device__ __forceinline__ int lean_ipad(int p) { return p + ((p >> 4) << 1); }   // 16-bit arrays
 
@@ -454,7 +474,12 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
             key[i] = KO::to_key(v[i]);
         }
     }
-    if (t == 0) s.emin = 0x7fffffff;
+    if (t == 0) {
+        s.emin = 0x7fffffff;
+        s.kmin = ~(K)0;
+        s.kmax = 0;
+        s.bmax = 0;
+    }
     if (__syncthreads_or(bad)) {
         if (t == 0) ws_flag(status, WS_STATUS_NONFINITE);
         return;
@@ -480,7 +505,6 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     // distributions of weights a bucket holds a few elements.  If a bucket is
     // larger than BUCKET_MAX the segment takes the LSD radix passes instead.
     constexpr int BUCKET_MAX = 32;
-    if (t == 0) { s.kmin = ~(K)0; s.kmax = 0; s.bmax = 0; }
     {
         K lo = ~(K)0, hi = 0;
 #pragma unroll
@@ -493,7 +517,6 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
         }
         int* cnt = s.u.bucket.cnt;
         for (int i = t; i < n; i += NT) cnt[kpad(i)] = 0;
-        __syncthreads();
         if (l == 0) { ws_atomic_min_k(&s.kmin, lo); ws_atomic_max_k(&s.kmax, hi); }
     }
     __syncthreads();
@@ -539,7 +562,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
             big = max(big, c[i]);
         }
         int tot;
-        int run = ws_block_excl_scan<NT, int>(sum, s.wsumi, &tot);
+        int run = lean_excl_scan(sum, s.wsumi, &tot);
 #pragma unroll
         for (int i = 0; i < M; ++i)
             if (first + i < n) { cnt[kpad(first + i)] = run; run += c[i]; }
@@ -708,7 +731,7 @@ __global__ void __launch_bounds__(wsh::NT, sizeof(T) == 4 ? 3 : 2) k_small(const
     // ---- cluster ids: rank of every start; values of the clusters this thread starts
     const uint32_t mine = (uint32_t)st16[t] & (first < n ? (n - first >= M ? 0xffffu : ((1u << (n - first)) - 1u)) : 0u);
     int C;
-    const int base = ws_block_excl_scan<NT, int>(__popc(mine), h.wsum, &C);
+    const int base = lean_excl_scan(__popc(mine), h.wsum, &C);
     const float x0f = (float)xlo;
     {
         uint32_t rest = mine;
