@@ -689,14 +689,15 @@ __device__ __forceinline__ int ws_bucket(float x, float lo, float scale, int nb)
 }
 
 // ---------------------------------------------------------------------------
-// 5. cluster table + directory fill (one CTA per hull tile)
+// 5. cluster table + directory fill (one CTA per hull tile; eight CTAs per
+//    SM at 32 registers: its reads are latency bound, so warps beat registers)
 // ---------------------------------------------------------------------------
 constexpr int GAP_INLINE = 64;
 
 struct BigGap { int64_t pos; int32_t count; int32_t value; uint32_t key32; int32_t pad; };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_table(const TileDesc* __restrict__ htiles, const LargeSeg* __restrict__ lsegs,
+__global__ void __launch_bounds__(256, 8) k_table(const TileDesc* __restrict__ htiles, const LargeSeg* __restrict__ lsegs,
                                                const double* __restrict__ lambdas, const SegRuntime* __restrict__ rt,
                                                const typename KeyOf<T>::K* __restrict__ sorted,
                                                const uint16_t* __restrict__ vp, const i128* __restrict__ vx,
