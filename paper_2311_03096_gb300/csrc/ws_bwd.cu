@@ -12,10 +12,18 @@
 // (one rounding when the mean is formed).
 //
 // Large segments: per-segment scale and largest id (k_bwd_prep), the used
-// cluster slots cleared (k_bwd_zero), the sums (k_bwd_accum: lanes of a warp
-// with the same cluster add once, and a tile whose elements all share one
-// cluster adds once per CTA, so a single huge cluster costs one atomic per
-// sort tile), the means (k_bwd_mean), the gather (k_bwd_apply).
+// cluster slots cleared (k_bwd_zero), the sums, the means (k_bwd_mean), the
+// gather (k_bwd_apply).  The sums: the cluster slots are cut into buckets of
+// 2^s consecutive slots, small enough for L2; k_bwd_scatter writes every
+// element as a pair (slot within its bucket, exact fixed-point code) into its
+// bucket's region (the regions sized by k_bwd_prep's bucket counts), and
+// k_bwd_pairs walks the pairs bucket by bucket on a persistent grid, so the
+// atomics of the CTAs in flight fall into one or two buckets' slots and stay
+// in L2 instead of each costing a random DRAM read and write.  Lanes of a
+// warp with the same slot add once, and a sort tile whose elements all share
+// one cluster adds once per CTA (no pairs), so a single huge cluster costs
+// one atomic per sort tile.  The pairs and the bucket counters borrow the
+// forward's sort buffers, which the backward does not otherwise use.
 // One-CTA segments: the same arithmetic in shared memory (k_small_backward).
 #include "ws_kernels.cuh"
 
@@ -53,6 +61,38 @@ __device__ __forceinline__ T ws_bwd_mean(i128 S, int cnt, int emax) {
     return (T)ldexp(ws_div_i128_n(S, cnt), -Lg);
 }
 
+// A ws_bwd_fix value in one word of the key's width: the significand m
+// (MANT + 1 bits, implicit bit included), the shift sh + MANT + 1 in 7 bits
+// (sh <= SH, and shifts below -(MANT + 1) give 0, stored as m = 0), the sign
+// on top.  Decoding gives back ws_bwd_fix(g, emax) exactly, with no segment
+// at hand.
+template <typename T>
+__device__ __forceinline__ typename KeyOf<T>::K ws_bwd_encode(T g, int emax) {
+    typedef KeyOf<T> KO;
+    typedef typename KO::K K;
+    constexpr int MB = KO::MANT + 1;
+    const uint64_t b = (uint64_t)KO::bits(g);
+    int e = (int)((b >> KO::MANT) & KO::EXPMASK);
+    uint64_t m = b & ((1ull << KO::MANT) - 1ull);
+    if (e == 0) e = 1; else m |= (1ull << KO::MANT);
+    int sh = e - emax + BwdFix<T>::SH;
+    if (sh < -MB) { m = 0; sh = 0; }
+    const uint64_t neg = (b >> (KO::BITS - 1)) & 1ull;
+    return (K)((neg << (KO::BITS - 1)) | ((uint64_t)(sh + MB) << MB) | m);
+}
+template <typename T>
+__device__ __forceinline__ i128 ws_bwd_decode(typename KeyOf<T>::K c) {
+    typedef KeyOf<T> KO;
+    constexpr int MB = KO::MANT + 1;
+    const uint64_t w = (uint64_t)c;
+    const uint64_t m = w & ((1ull << MB) - 1ull);
+    const int sh = (int)((w >> MB) & 127u) - MB;
+    const u128 mag = sh >= 0 ? (u128)m << sh : (u128)(m >> (-sh));
+    return ((w >> (KO::BITS - 1)) & 1ull) ? -(i128)mag : (i128)mag;
+}
+
+constexpr int BK_MAX = 256;   // slot buckets at most
+
 __device__ __forceinline__ void ws_atomic_add_i128(unsigned long long* lo_hi, i128 v) {
     const unsigned long long lo = (unsigned long long)(uint64_t)v;
     const unsigned long long hi = (unsigned long long)(uint64_t)((u128)v >> 64);
@@ -80,21 +120,36 @@ __device__ __forceinline__ i128 ws_group_sum_i96(unsigned peers, i128 v) {
 }
 
 // 1. per segment: largest exponent of grad_out and largest cluster id
+// and, for the tiles that are not one cluster, the number of elements in
+// every slot bucket
 template <typename T>
 __global__ void __launch_bounds__(BNT) k_bwd_prep(const T* __restrict__ g, const int32_t* __restrict__ ids,
                                                   const TileDesc* __restrict__ tiles,
                                                   const LargeSeg* __restrict__ lsegs, int32_t* seg_emax,
-                                                  int32_t* seg_maxid, uint32_t* status) {
+                                                  int32_t* seg_maxid, int nb, int s, unsigned long long* bk_cnt,
+                                                  uint32_t* status) {
+    __shared__ int h[BK_MAX];
     const TileDesc td = tiles[blockIdx.x];
     const LargeSeg ls = lsegs[td.lseg];
+    const int64_t slot0 = ls.kpos + td.lseg;
+    for (int b = threadIdx.x; b < nb; b += BNT) h[b] = 0;
+    __syncthreads();
+    const int id0 = ids[td.vpos];
     int e = 0, mx = -1;
-    bool bad = false;
+    bool bad = false, same = true;
     for (int i = threadIdx.x; i < td.len; i += BNT) {
         e = max(e, ws_g_exp(g[td.vpos + i]));
         const int id = ids[td.vpos + i];
+        same &= id == id0;
         if (id < 0 || (int64_t)id >= ls.len) bad = true;
-        else mx = max(mx, id);
+        else {
+            mx = max(mx, id);
+            atomicAdd(&h[(int)((slot0 + id) >> s)], 1);
+        }
     }
+    if (!__syncthreads_and(same))
+        for (int b = threadIdx.x; b < nb; b += BNT)
+            if (h[b]) atomicAdd(bk_cnt + b, (unsigned long long)h[b]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
@@ -124,30 +179,54 @@ __global__ void __launch_bounds__(BNT) k_bwd_zero(const TileDesc* __restrict__ t
     }
 }
 
-// 3. exact cluster sums
+// 3a. bucket regions: exclusive prefix of the counts (one thread; at most
+// BK_MAX buckets), and the scatter cursors
+__global__ void k_bwd_bscan(const unsigned long long* __restrict__ bk_cnt, int nb, unsigned long long* bk_off,
+                            unsigned long long* bk_cur) {
+    if (threadIdx.x != 0) return;
+    unsigned long long run = 0;
+    for (int b = 0; b < nb; ++b) {
+        bk_off[b] = run;
+        bk_cur[b] = run;
+        run += bk_cnt[b];
+    }
+    bk_off[nb] = run;
+}
+
+// 3b. a tile that is one cluster adds its exact sum once; every other tile
+// writes its elements as (slot within bucket, code) pairs into the bucket
+// regions
 template <typename T>
-__global__ void __launch_bounds__(BNT) k_bwd_accum(const T* __restrict__ g, const int32_t* __restrict__ ids,
-                                                   const TileDesc* __restrict__ tiles,
-                                                   const LargeSeg* __restrict__ lsegs,
-                                                   const int32_t* __restrict__ seg_emax, unsigned long long* acc,
-                                                   int32_t* cnt) {
+__global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, const int32_t* __restrict__ ids,
+                                                     const TileDesc* __restrict__ tiles,
+                                                     const LargeSeg* __restrict__ lsegs,
+                                                     const int32_t* __restrict__ seg_emax, unsigned long long* acc,
+                                                     int32_t* cnt, int nb, int s, unsigned long long* bk_cur,
+                                                     int32_t* pslot, typename KeyOf<T>::K* pcode) {
     __shared__ long long wlo[BNT / 32], whi[BNT / 32];
+    __shared__ int h[BK_MAX];
+    __shared__ unsigned long long base[BK_MAX];
     const TileDesc td = tiles[blockIdx.x];
     const LargeSeg ls = lsegs[td.lseg];
     const int64_t slot0 = ls.kpos + td.lseg;
     const int emax = seg_emax[td.lseg];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     auto valid_id = [&](int id) { return id >= 0 && (int64_t)id < ls.len; };
-    // a tile whose elements all share one cluster adds its sum once
+    for (int b = t; b < nb; b += BNT) h[b] = 0;
+    __syncthreads();
     const int id0 = ids[td.vpos];
     bool same = true;
-    for (int i = t; i < td.len; i += BNT) same &= ids[td.vpos + i] == id0;
+    for (int i = t; i < td.len; i += BNT) {
+        const int id = ids[td.vpos + i];
+        same &= id == id0;
+        if (valid_id(id)) atomicAdd(&h[(int)((slot0 + id) >> s)], 1);
+    }
     if (__syncthreads_and(same)) {
         if (!valid_id(id0)) return;
-        i128 s = 0;
-        for (int i = t; i < td.len; i += BNT) s += ws_bwd_fix<T>(g[td.vpos + i], emax);
-        s = ws_warp_reduce_i128(s);
-        if (lane == 0) { wlo[w] = (long long)(uint64_t)s; whi[w] = (long long)(uint64_t)((u128)s >> 64); }
+        i128 sum = 0;
+        for (int i = t; i < td.len; i += BNT) sum += ws_bwd_fix<T>(g[td.vpos + i], emax);
+        sum = ws_warp_reduce_i128(sum);
+        if (lane == 0) { wlo[w] = (long long)(uint64_t)sum; whi[w] = (long long)(uint64_t)((u128)sum >> 64); }
         __syncthreads();
         if (t == 0) {
             i128 tot = 0;
@@ -157,18 +236,68 @@ __global__ void __launch_bounds__(BNT) k_bwd_accum(const T* __restrict__ g, cons
         }
         return;
     }
-    // otherwise: lanes of a warp holding the same cluster add their sum once
-    for (int i0 = 0; i0 < td.len; i0 += BNT) {
-        const int i = i0 + t;
-        const bool in = i < td.len;
-        const int id = in ? ids[td.vpos + i] : -1;
-        const i128 q = in ? ws_bwd_fix<T>(g[td.vpos + i], emax) : (i128)0;
-        const unsigned peers = __match_any_sync(0xffffffffu, id);
-        const int leader = __ffs((int)peers) - 1;
-        const i128 s = __any_sync(0xffffffffu, __popc(peers) > 1) ? ws_group_sum_i96(peers, q) : q;
-        if (in && lane == leader && valid_id(id)) {
-            ws_atomic_add_i128(acc + 2 * (slot0 + id), s);
-            atomicAdd(cnt + slot0 + id, __popc(peers));
+    for (int b = t; b < nb; b += BNT) {
+        const int c = h[b];
+        base[b] = c ? atomicAdd(bk_cur + b, (unsigned long long)c) : 0ull;
+        h[b] = 0;
+    }
+    __syncthreads();
+    const int64_t low = ((int64_t)1 << s) - 1;
+    for (int i = t; i < td.len; i += BNT) {
+        const int id = ids[td.vpos + i];
+        if (!valid_id(id)) continue;
+        const int64_t slot = slot0 + id;
+        const int b = (int)(slot >> s);
+        const unsigned long long pos = base[b] + (unsigned long long)atomicAdd(&h[b], 1);
+        pslot[pos] = (int32_t)(slot & low);
+        pcode[pos] = ws_bwd_encode<T>(g[td.vpos + i], emax);
+    }
+}
+
+// 3c. the pairs, bucket by bucket: a persistent grid walks them in order, so
+// the slots that the CTAs in flight add into span about one bucket
+constexpr int BPER = 8;   // pairs per thread and step
+
+template <typename T>
+__global__ void __launch_bounds__(BNT) k_bwd_pairs(const int32_t* __restrict__ pslot,
+                                                   const typename KeyOf<T>::K* __restrict__ pcode,
+                                                   const unsigned long long* __restrict__ bk_off, int nb, int s,
+                                                   unsigned long long* acc, int32_t* cnt) {
+    typedef typename KeyOf<T>::K K;
+    __shared__ unsigned long long off[BK_MAX + 1];
+    for (int b = threadIdx.x; b <= nb; b += BNT) off[b] = bk_off[b];
+    __syncthreads();
+    const unsigned long long total = off[nb];
+    const int lane = threadIdx.x & 31;
+    constexpr unsigned long long CH = (unsigned long long)BNT * BPER;
+    int b = 0;   // bucket of this thread's current pair (pairs only move forward)
+    for (unsigned long long c0 = (unsigned long long)blockIdx.x * CH; c0 < total;
+         c0 += (unsigned long long)gridDim.x * CH) {
+        int32_t sl[BPER];
+        K cd[BPER];
+#pragma unroll
+        for (int k = 0; k < BPER; ++k) {
+            const unsigned long long j = c0 + (unsigned long long)k * BNT + threadIdx.x;
+            sl[k] = j < total ? pslot[j] : 0;
+            cd[k] = j < total ? pcode[j] : (K)0;
+        }
+#pragma unroll
+        for (int k = 0; k < BPER; ++k) {
+            const unsigned long long j = c0 + (unsigned long long)k * BNT + threadIdx.x;
+            const bool in = j < total;
+            long long slot = -1 - lane;   // distinct for lanes past the end
+            i128 v = 0;
+            if (in) {
+                while (b + 1 < nb && off[b + 1] <= j) ++b;
+                slot = ((long long)b << s) | (long long)sl[k];
+                v = ws_bwd_decode<T>(cd[k]);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)slot);
+            const i128 sum = __any_sync(0xffffffffu, __popc(peers) > 1) ? ws_group_sum_i96(peers, v) : v;
+            if (in && lane == __ffs((int)peers) - 1) {
+                ws_atomic_add_i128(acc + 2 * slot, sum);
+                atomicAdd(cnt + slot, __popc(peers));
+            }
         }
     }
 }
@@ -297,11 +426,45 @@ cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* 
     e = cudaMemsetAsync(seg_maxid, 0xff, sizeof(int32_t) * W.n_lseg, st);
     if (e) return e;
     const int nt = W.n_sort_tiles;
+    // slot buckets of 2^s slots (2^21 slots of 20 bytes: about 40 MB, well
+    // inside L2); their counters live in the sort histogram buffer, which
+    // holds at least 3 nb + 1 words for the nb allowed here
+    typedef typename KeyOf<T>::K K;
+    constexpr int P = KeyOf<T>::BITS / 8;
+    const int64_t total_slots = W.n_keys + W.n_lseg;
+    const int64_t words = (int64_t)sizeof(uint32_t) * W.n_lseg * P * 256 / sizeof(unsigned long long);
+    const int nb_max = (int)std::min<int64_t>(BK_MAX, (words - 1) / 3);
+    int s = 21;
+    while (((total_slots + ((int64_t)1 << s) - 1) >> s) > nb_max) ++s;
+    const int nb = (int)((total_slots + ((int64_t)1 << s) - 1) >> s);
+    unsigned long long* bk_cnt = reinterpret_cast<unsigned long long*>(W.hist);
+    unsigned long long* bk_off = bk_cnt + nb;
+    unsigned long long* bk_cur = bk_off + nb + 1;
+    // the pairs borrow the sort's key buffers (n_keys entries each)
+    int32_t* pslot = reinterpret_cast<int32_t*>(W.keys_a);
+    K* pcode = W.keys_b;
+    e = cudaMemsetAsync(bk_cnt, 0, sizeof(unsigned long long) * nb, st);
+    if (e) return e;
+    static const int pairs_grid = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_pairs<T>, BNT, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 4 * 152;
+        }
+        return std::max(1, sms * std::max(per_sm, 1));
+    }();
     WS_LAUNCH(W.prof, WSK_BWD, st,
-              (k_bwd_prep<T><<<nt, BNT, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, seg_maxid, status)));
+              (k_bwd_prep<T><<<nt, BNT, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, seg_maxid, nb, s, bk_cnt,
+                                                 status)));
     WS_LAUNCH(W.prof, WSK_BWD, st, (k_bwd_zero<<<nt, BNT, 0, st>>>(W.sort_tiles, W.lsegs, seg_maxid, W.bacc, W.bcnt)));
+    WS_LAUNCH(W.prof, WSK_BWD, st, (k_bwd_bscan<<<1, 32, 0, st>>>(bk_cnt, nb, bk_off, bk_cur)));
     WS_LAUNCH(W.prof, WSK_BWD, st,
-              (k_bwd_accum<T><<<nt, BNT, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, W.bacc, W.bcnt)));
+              (k_bwd_scatter<T><<<nt, BNT, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, W.bacc, W.bcnt, nb, s,
+                                                    bk_cur, pslot, pcode)));
+    WS_LAUNCH(W.prof, WSK_BWD, st,
+              (k_bwd_pairs<T><<<pairs_grid, BNT, 0, st>>>(pslot, pcode, bk_off, nb, s, W.bacc, W.bcnt)));
     WS_LAUNCH(W.prof, WSK_BWD, st,
               (k_bwd_mean<T><<<nt, BNT, 0, st>>>(W.sort_tiles, W.lsegs, seg_maxid, seg_emax, W.bacc, W.bcnt,
                                                  W.bsum)));

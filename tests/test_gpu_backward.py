@@ -93,3 +93,30 @@ def test_backward_cancellation_is_exact(ws, ctx, small):
     for s in range(n_seg):
         want = np.float32(3 + s) / np.float32(n)   # one correctly rounded FP32 division
         assert np.all(gin[s * n:(s + 1) * n] == want), (s, gin[s * n], want)
+
+
+@pytest.mark.parametrize("dt,np_dt", [(torch.float32, np.float32), (torch.float64, np.float64)])
+def test_backward_exact_sums_scattered_clusters(ws, ctx, dt, np_dt):
+    # ids chosen by hand (the backward holds any partition fixed): cluster c
+    # holds every element i = c (mod 1000), so every tile mixes a thousand
+    # clusters and the sums go through the bucketed pairs, with warps adding
+    # neighbours of one cluster together.  grad_out: +-2^40 pairs in every
+    # cluster and, where the cluster size is odd, one small integer c mod 7 in
+    # place of the unpaired +2^40; each sum is exactly that integer.
+    d, ncl = (1 << 22) + 77, 1000
+    i = np.arange(d)
+    c, k = i % ncl, i // ncl
+    size = (d - np.arange(ncl) + ncl - 1) // ncl
+    g = np.where(k % 2 == 0, 2.0 ** 40, -(2.0 ** 40)).astype(np_dt)
+    last_odd = (k == size[c] - 1) & (size[c] % 2 == 1)
+    g[last_odd] = (c[last_odd] % 7).astype(np_dt)
+    ids = c.astype(np.int32)
+    gin = ws.prox_backward(torch.from_numpy(g).cuda(), torch.from_numpy(ids).cuda()).cpu().numpy()
+    ctx.check(what="backward")
+    tot = np.where(size % 2 == 1, np.arange(ncl) % 7, 0)
+    if dt == torch.float32:
+        want = (tot.astype(np.float32) / size.astype(np.float32))[c]   # one correctly rounded division
+        assert np.array_equal(gin, want)
+    else:
+        want = (tot / size)[c]
+        assert np.all(np.abs(gin - want) <= 1e-12 * np.abs(want))
