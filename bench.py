@@ -446,6 +446,30 @@ def run_rows_case(args):
     print(json.dumps({"case": "rows", "segments": int(len(lam)), "elements": int(off[-1]), "ms_per_call": ms}))
 
 
+def run_backward_case(args):
+    """The device-wide backward alone at d (FP32, lambda --lam): one forward for
+    the cluster ids, then warm-up + steps backward calls, CUDA-event time of the
+    steps -- the launches that the backward's profiles capture."""
+    import torch
+
+    import __graft_entry__
+    from paper_2311_03096_gb300 import inputs, ws
+
+    __graft_entry__.build()
+    ctx = ws.Context.get(0)
+    stream = torch.cuda.current_stream()
+    w = torch.from_numpy(inputs.normal_with_duplicates(args.d, seed=args.seed, dtype=np.float32)).cuda()
+    g = torch.from_numpy(inputs.normal(args.d, seed=args.seed + 1, dtype=np.float32)).cuda()
+    gin = torch.empty_like(g)
+    _, ids, nc = ws.prox(w, args.lam, args.prec, ctx=ctx)
+    for _ in range(args.warmup):
+        ws.prox_backward(g, ids, ctx=ctx, grad_in=gin)
+    ms = _time_calls(lambda: ws.prox_backward(g, ids, ctx=ctx, grad_in=gin), stream, max(args.steps, 1))
+    ctx.check(what="backward case")
+    print(json.dumps({"case": "backward", "d": args.d, "lambda": args.lam, "clusters": int(nc.item()),
+                      "ms_per_call": ms}))
+
+
 def config_dict(args, world):
     return {"workload": WORKLOAD, "d": args.d, "lambdas": list(LAMBDAS), "storage": "f32", "prec": args.prec,
             "arithmetic": "merge decisions exact in 64/128-bit fixed point; cluster values in "
@@ -466,9 +490,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--case", default="single", choices=["single", "rows"],
+    ap.add_argument("--case", default="single", choices=["single", "rows", "backward"],
                     help="rows: only run the batched MLP rows forward (warm-up + steps calls) and print its "
-                         "ms per call -- the launch that the one-CTA kernel's profiles capture")
+                         "ms per call -- the launch that the one-CTA kernel's profiles capture; backward: "
+                         "only the device-wide backward at --d and --lam")
+    ap.add_argument("--lam", type=float, default=1e-2, help="lambda of --case backward")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -477,6 +503,9 @@ def main():
         return
     if args.case == "rows":
         run_rows_case(args)
+        return
+    if args.case == "backward":
+        run_backward_case(args)
         return
 
     import torch
