@@ -180,10 +180,11 @@ __global__ void __launch_bounds__(BNT) k_bwd_zero(const TileDesc* __restrict__ t
 }
 
 // 3a. bucket regions: exclusive prefix of the counts (one thread; at most
-// BK_MAX buckets), and the scatter cursors
+// BK_MAX buckets), the scatter cursors and the pairs pass's chunk counter
 __global__ void k_bwd_bscan(const unsigned long long* __restrict__ bk_cnt, int nb, unsigned long long* bk_off,
                             unsigned long long* bk_cur) {
     if (threadIdx.x != 0) return;
+    bk_cur[nb] = 0ull;
     unsigned long long run = 0;
     for (int b = 0; b < nb; ++b) {
         bk_off[b] = run;
@@ -254,25 +255,32 @@ __global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, co
     }
 }
 
-// 3c. the pairs, bucket by bucket: a persistent grid walks them in order, so
-// the slots that the CTAs in flight add into span about one bucket
+// 3c. the pairs, bucket by bucket: the CTAs of a persistent grid take chunks
+// in order from a counter (not a fixed stride, which lets CTAs drift apart),
+// so the slots that the chunks in flight add into span about one bucket
 constexpr int BPER = 8;   // pairs per thread and step
 
 template <typename T>
 __global__ void __launch_bounds__(BNT) k_bwd_pairs(const int32_t* __restrict__ pslot,
                                                    const typename KeyOf<T>::K* __restrict__ pcode,
                                                    const unsigned long long* __restrict__ bk_off, int nb, int s,
-                                                   unsigned long long* acc, int32_t* cnt) {
+                                                   unsigned long long* chunk_ctr, unsigned long long* acc,
+                                                   int32_t* cnt) {
     typedef typename KeyOf<T>::K K;
     __shared__ unsigned long long off[BK_MAX + 1];
+    __shared__ unsigned long long s_c0;
     for (int b = threadIdx.x; b <= nb; b += BNT) off[b] = bk_off[b];
     __syncthreads();
     const unsigned long long total = off[nb];
     const int lane = threadIdx.x & 31;
     constexpr unsigned long long CH = (unsigned long long)BNT * BPER;
     int b = 0;   // bucket of this thread's current pair (pairs only move forward)
-    for (unsigned long long c0 = (unsigned long long)blockIdx.x * CH; c0 < total;
-         c0 += (unsigned long long)gridDim.x * CH) {
+    while (true) {
+        __syncthreads();   // every thread has read the previous chunk's start
+        if (threadIdx.x == 0) s_c0 = atomicAdd(chunk_ctr, 1ull) * CH;
+        __syncthreads();
+        const unsigned long long c0 = s_c0;
+        if (c0 >= total) break;
         int32_t sl[BPER];
         K cd[BPER];
 #pragma unroll
@@ -428,18 +436,18 @@ cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* 
     const int nt = W.n_sort_tiles;
     // slot buckets of 2^s slots (2^21 slots of 20 bytes: about 40 MB, well
     // inside L2); their counters live in the sort histogram buffer, which
-    // holds at least 3 nb + 1 words for the nb allowed here
+    // holds at least 3 nb + 2 words for the nb allowed here
     typedef typename KeyOf<T>::K K;
     constexpr int P = KeyOf<T>::BITS / 8;
     const int64_t total_slots = W.n_keys + W.n_lseg;
     const int64_t words = (int64_t)sizeof(uint32_t) * W.n_lseg * P * 256 / sizeof(unsigned long long);
-    const int nb_max = (int)std::min<int64_t>(BK_MAX, (words - 1) / 3);
+    const int nb_max = (int)std::min<int64_t>(BK_MAX, (words - 2) / 3);
     int s = 21;
     while (((total_slots + ((int64_t)1 << s) - 1) >> s) > nb_max) ++s;
     const int nb = (int)((total_slots + ((int64_t)1 << s) - 1) >> s);
     unsigned long long* bk_cnt = reinterpret_cast<unsigned long long*>(W.hist);
     unsigned long long* bk_off = bk_cnt + nb;
-    unsigned long long* bk_cur = bk_off + nb + 1;
+    unsigned long long* bk_cur = bk_off + nb + 1;   // nb cursors, then the chunk counter
     // the pairs borrow the sort's key buffers (n_keys entries each)
     int32_t* pslot = reinterpret_cast<int32_t*>(W.keys_a);
     K* pcode = W.keys_b;
@@ -464,7 +472,8 @@ cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* 
               (k_bwd_scatter<T><<<nt, BNT, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, W.bacc, W.bcnt, nb, s,
                                                     bk_cur, pslot, pcode)));
     WS_LAUNCH(W.prof, WSK_BWD, st,
-              (k_bwd_pairs<T><<<pairs_grid, BNT, 0, st>>>(pslot, pcode, bk_off, nb, s, W.bacc, W.bcnt)));
+              (k_bwd_pairs<T><<<pairs_grid, BNT, 0, st>>>(pslot, pcode, bk_off, nb, s, bk_cur + nb, W.bacc,
+                                                          W.bcnt)));
     WS_LAUNCH(W.prof, WSK_BWD, st,
               (k_bwd_mean<T><<<nt, BNT, 0, st>>>(W.sort_tiles, W.lsegs, seg_maxid, seg_emax, W.bacc, W.bcnt,
                                                  W.bsum)));
