@@ -92,6 +92,7 @@ __device__ __forceinline__ i128 ws_bwd_decode(typename KeyOf<T>::K c) {
 }
 
 constexpr int BK_MAX = 256;   // slot buckets at most
+constexpr int BL = 8;         // elements per thread whose loads are issued together (prep, scatter)
 
 __device__ __forceinline__ void ws_atomic_add_i128(unsigned long long* lo_hi, i128 v) {
     const unsigned long long lo = (unsigned long long)(uint64_t)v;
@@ -137,14 +138,26 @@ __global__ void __launch_bounds__(BNT) k_bwd_prep(const T* __restrict__ g, const
     const int id0 = ids[td.vpos];
     int e = 0, mx = -1;
     bool bad = false, same = true;
-    for (int i = threadIdx.x; i < td.len; i += BNT) {
-        e = max(e, ws_g_exp(g[td.vpos + i]));
-        const int id = ids[td.vpos + i];
-        same &= id == id0;
-        if (id < 0 || (int64_t)id >= ls.len) bad = true;
-        else {
-            mx = max(mx, id);
-            atomicAdd(&h[(int)((slot0 + id) >> s)], 1);
+    for (int i0 = threadIdx.x; i0 < td.len; i0 += BNT * BL) {
+        int idv[BL];
+        T gv[BL];
+#pragma unroll
+        for (int k = 0; k < BL; ++k) {   // (indices clamped into the tile: every load in bounds)
+            const int i = min(i0 + k * BNT, td.len - 1);
+            idv[k] = ids[td.vpos + i];
+            gv[k] = g[td.vpos + i];
+        }
+#pragma unroll
+        for (int k = 0; k < BL; ++k) {
+            if (i0 + k * BNT >= td.len) continue;
+            e = max(e, ws_g_exp(gv[k]));
+            const int id = idv[k];
+            same &= id == id0;
+            if (id < 0 || (int64_t)id >= ls.len) bad = true;
+            else {
+                mx = max(mx, id);
+                atomicAdd(&h[(int)((slot0 + id) >> s)], 1);
+            }
         }
     }
     if (!__syncthreads_and(same))
@@ -217,10 +230,16 @@ __global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, co
     __syncthreads();
     const int id0 = ids[td.vpos];
     bool same = true;
-    for (int i = t; i < td.len; i += BNT) {
-        const int id = ids[td.vpos + i];
-        same &= id == id0;
-        if (valid_id(id)) atomicAdd(&h[(int)((slot0 + id) >> s)], 1);
+    for (int i0 = t; i0 < td.len; i0 += BNT * BL) {
+        int idv[BL];
+#pragma unroll
+        for (int k = 0; k < BL; ++k) idv[k] = ids[td.vpos + min(i0 + k * BNT, td.len - 1)];
+#pragma unroll
+        for (int k = 0; k < BL; ++k) {
+            if (i0 + k * BNT >= td.len) continue;
+            same &= idv[k] == id0;
+            if (valid_id(idv[k])) atomicAdd(&h[(int)((slot0 + idv[k]) >> s)], 1);
+        }
     }
     if (__syncthreads_and(same)) {
         if (!valid_id(id0)) return;
@@ -244,14 +263,24 @@ __global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, co
     }
     __syncthreads();
     const int64_t low = ((int64_t)1 << s) - 1;
-    for (int i = t; i < td.len; i += BNT) {
-        const int id = ids[td.vpos + i];
-        if (!valid_id(id)) continue;
-        const int64_t slot = slot0 + id;
-        const int b = (int)(slot >> s);
-        const unsigned long long pos = base[b] + (unsigned long long)atomicAdd(&h[b], 1);
-        pslot[pos] = (int32_t)(slot & low);
-        pcode[pos] = ws_bwd_encode<T>(g[td.vpos + i], emax);
+    for (int i0 = t; i0 < td.len; i0 += BNT * BL) {
+        int idv[BL];
+        T gv[BL];
+#pragma unroll
+        for (int k = 0; k < BL; ++k) {
+            const int i = min(i0 + k * BNT, td.len - 1);
+            idv[k] = ids[td.vpos + i];
+            gv[k] = g[td.vpos + i];
+        }
+#pragma unroll
+        for (int k = 0; k < BL; ++k) {
+            if (i0 + k * BNT >= td.len || !valid_id(idv[k])) continue;
+            const int64_t slot = slot0 + idv[k];
+            const int b = (int)(slot >> s);
+            const unsigned long long pos = base[b] + (unsigned long long)atomicAdd(&h[b], 1);
+            pslot[pos] = (int32_t)(slot & low);
+            pcode[pos] = ws_bwd_encode<T>(gv[k], emax);
+        }
     }
 }
 
