@@ -209,7 +209,12 @@ __global__ void k_bwd_bscan(const unsigned long long* __restrict__ bk_cnt, int n
 
 // 3b. a tile that is one cluster adds its exact sum once; every other tile
 // writes its elements as (slot within bucket, code) pairs into the bucket
-// regions
+// regions: first into shared memory grouped by bucket, then each bucket's
+// run copied out to consecutive addresses (whole sectors, not one 4-byte
+// store per scattered element)
+template <typename T>
+size_t ws_bwd_scatter_smem() { return (size_t)BTILE * (sizeof(int32_t) + sizeof(typename KeyOf<T>::K) + 1); }
+
 template <typename T>
 __global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, const int32_t* __restrict__ ids,
                                                      const TileDesc* __restrict__ tiles,
@@ -217,9 +222,15 @@ __global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, co
                                                      const int32_t* __restrict__ seg_emax, unsigned long long* acc,
                                                      int32_t* cnt, int nb, int s, unsigned long long* bk_cur,
                                                      int32_t* pslot, typename KeyOf<T>::K* pcode) {
+    typedef typename KeyOf<T>::K K;
     __shared__ long long wlo[BNT / 32], whi[BNT / 32];
-    __shared__ int h[BK_MAX];
+    __shared__ int h[BK_MAX], lstart[BK_MAX], wsum[BNT / 32];
     __shared__ unsigned long long base[BK_MAX];
+    extern __shared__ __align__(16) unsigned char stage_raw[];
+    int32_t* st_slot = reinterpret_cast<int32_t*>(stage_raw);               // [BTILE]
+    K* st_code = reinterpret_cast<K*>(stage_raw + sizeof(int32_t) * BTILE);  // [BTILE]
+    uint8_t* st_b = stage_raw + (sizeof(int32_t) + sizeof(K)) * BTILE;      // [BTILE] bucket (nb <= 256)
+    static_assert(BK_MAX <= BNT && BK_MAX <= 256, "one thread per bucket; buckets fit a byte");
     const TileDesc td = tiles[blockIdx.x];
     const LargeSeg ls = lsegs[td.lseg];
     const int64_t slot0 = ls.kpos + td.lseg;
@@ -244,7 +255,14 @@ __global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, co
     if (__syncthreads_and(same)) {
         if (!valid_id(id0)) return;
         i128 sum = 0;
-        for (int i = t; i < td.len; i += BNT) sum += ws_bwd_fix<T>(g[td.vpos + i], emax);
+        for (int i0 = t; i0 < td.len; i0 += BNT * BL) {
+            T gv[BL];
+#pragma unroll
+            for (int k = 0; k < BL; ++k) gv[k] = g[td.vpos + min(i0 + k * BNT, td.len - 1)];
+#pragma unroll
+            for (int k = 0; k < BL; ++k)
+                if (i0 + k * BNT < td.len) sum += ws_bwd_fix<T>(gv[k], emax);
+        }
         sum = ws_warp_reduce_i128(sum);
         if (lane == 0) { wlo[w] = (long long)(uint64_t)sum; whi[w] = (long long)(uint64_t)((u128)sum >> 64); }
         __syncthreads();
@@ -256,10 +274,14 @@ __global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, co
         }
         return;
     }
-    for (int b = t; b < nb; b += BNT) {
-        const int c = h[b];
-        base[b] = c ? atomicAdd(bk_cur + b, (unsigned long long)c) : 0ull;
-        h[b] = 0;
+    // each bucket's run in the staging area and its region in the pairs
+    const int cb = t < nb ? h[t] : 0;
+    int total;
+    const int lb = ws_block_excl_scan<BNT, int>(cb, wsum, &total);
+    if (t < nb) {
+        lstart[t] = lb;
+        base[t] = cb ? atomicAdd(bk_cur + t, (unsigned long long)cb) : 0ull;
+        h[t] = 0;
     }
     __syncthreads();
     const int64_t low = ((int64_t)1 << s) - 1;
@@ -277,10 +299,18 @@ __global__ void __launch_bounds__(BNT) k_bwd_scatter(const T* __restrict__ g, co
             if (i0 + k * BNT >= td.len || !valid_id(idv[k])) continue;
             const int64_t slot = slot0 + idv[k];
             const int b = (int)(slot >> s);
-            const unsigned long long pos = base[b] + (unsigned long long)atomicAdd(&h[b], 1);
-            pslot[pos] = (int32_t)(slot & low);
-            pcode[pos] = ws_bwd_encode<T>(gv[k], emax);
+            const int lp = lstart[b] + atomicAdd(&h[b], 1);
+            st_slot[lp] = (int32_t)(slot & low);
+            st_code[lp] = ws_bwd_encode<T>(gv[k], emax);
+            st_b[lp] = (uint8_t)b;
         }
+    }
+    __syncthreads();
+    for (int j = t; j < total; j += BNT) {
+        const int b = st_b[j];
+        const unsigned long long pos = base[b] + (unsigned long long)(j - lstart[b]);
+        pslot[pos] = st_slot[j];
+        pcode[pos] = st_code[j];
     }
 }
 
@@ -497,8 +527,11 @@ cudaError_t ws_large_backward(const LargeWork<T>& W, const T* g, const int32_t* 
                                                  status)));
     WS_LAUNCH(W.prof, WSK_BWD, st, (k_bwd_zero<<<nt, BNT, 0, st>>>(W.sort_tiles, W.lsegs, seg_maxid, W.bacc, W.bcnt)));
     WS_LAUNCH(W.prof, WSK_BWD, st, (k_bwd_bscan<<<1, 32, 0, st>>>(bk_cnt, nb, bk_off, bk_cur)));
+    const size_t scatter_smem = ws_bwd_scatter_smem<T>();
+    e = cudaFuncSetAttribute(k_bwd_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem);
+    if (e) return e;
     WS_LAUNCH(W.prof, WSK_BWD, st,
-              (k_bwd_scatter<T><<<nt, BNT, 0, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, W.bacc, W.bcnt, nb, s,
+              (k_bwd_scatter<T><<<nt, BNT, scatter_smem, st>>>(g, ids, W.sort_tiles, W.lsegs, seg_emax, W.bacc, W.bcnt, nb, s,
                                                     bk_cur, pslot, pcode)));
     WS_LAUNCH(W.prof, WSK_BWD, st,
               (k_bwd_pairs<T><<<pairs_grid, BNT, 0, st>>>(pslot, pcode, bk_off, nb, s, bk_cur + nb, W.bacc,
