@@ -455,8 +455,10 @@ __global__ void __launch_bounds__(256) k_chord(const TileDesc* __restrict__ htil
     const size_t b = (size_t)gw * (HT + 1);
     const int64_t p0 = (int64_t)td.tin * HT;
     bool below = false;
-    for (int v = lane; v < nv; v += 32) {
-        if (*(volatile const int32_t*)(seg_below + td.lseg)) break;   // decided elsewhere
+    for (int v = lane, it = 0; v < nv; v += 32, ++it) {
+        // decided elsewhere?  (an L2 round trip: every eighth step only, so that
+        // the two tail tiles' thousands of vertices do not wait on it each step)
+        if ((it & 7) == 0 && *(volatile const int32_t*)(seg_below + td.lseg)) break;
         const int64_t pos = p0 + vp[b + v];
         if (pos == 0 || pos == ls.len) continue;
         if (ws_convex((i128)0, base + vx[b + v], Xd, 0, pos, ls.len, sc)) { below = true; break; }
