@@ -16,10 +16,12 @@
 // gather (k_bwd_apply).  The sums: the cluster slots are cut into buckets of
 // 2^s consecutive slots, small enough for L2; k_bwd_scatter writes every
 // element as a pair (slot within its bucket, exact fixed-point code) into its
-// bucket's region (the regions sized by k_bwd_prep's bucket counts), and
-// k_bwd_pairs walks the pairs bucket by bucket on a persistent grid, so the
-// atomics of the CTAs in flight fall into one or two buckets' slots and stay
-// in L2 instead of each costing a random DRAM read and write.  Lanes of a
+// bucket's region (the regions sized by k_bwd_prep's bucket counts; each
+// tile's pairs are grouped by bucket in shared memory first, so every run is
+// copied out whole), and the CTAs of k_bwd_pairs take chunks of pairs in
+// order from a counter, so the atomics of the chunks in flight fall into one
+// or two buckets' slots and stay in L2 instead of each costing a random DRAM
+// read and write.  Lanes of a
 // warp with the same slot add once, and a sort tile whose elements all share
 // one cluster adds once per CTA (no pairs), so a single huge cluster costs
 // one atomic per sort tile.  The pairs and the bucket counters borrow the
