@@ -611,6 +611,12 @@ __global__ void __launch_bounds__(HNT) k_climb(const TileDesc* __restrict__ htil
                                                const int32_t* __restrict__ seg_mode) {
     __shared__ ClimbSmem s;
     const int t = threadIdx.x;
+    // Most calls have no segment left for the tree: all threads check this
+    // CTA's tiles at once, instead of one tile per round trip in the loop below.
+    bool any = false;
+    for (int tile = blockIdx.x + t * gridDim.x; tile < n_hull; tile += HNT * gridDim.x)
+        any |= seg_mode[htiles[tile].lseg] == 2;
+    if (!__syncthreads_or(any)) return;
     for (int tile = blockIdx.x; tile < n_hull; tile += gridDim.x) {
     const TileDesc td = htiles[tile];
     if (seg_mode[td.lseg] != 2) continue;   // (uniform)
